@@ -1,0 +1,400 @@
+"""Benchmark of the fused non-orthogonal MRT pseudopotential step on GB300.
+
+Workload (the paper's method at scale, one domain per GPU): 256^3 periodic,
+Carnahan-Starling EOS (a = 0.5, b = 4, R = 1) at T = 0.5 T_c with the Maxwell
+coexistence densities, random sphere droplets (radii uniform in [10, 40],
+numpy seed 2306, liquid fraction >= 0.10) in vapour, surface-tension tuning
+kappa = 0.5, sigma = 0.1, FP32 populations.  The headline value is D3Q19
+MLUPS; the D3Q27 lattice is measured in the same run and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the domain
+(independent problems: weak scaling, no collective on the data path); the
+timed region is bracketed by barriers and the maximum over ranks is used.
+Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step)"
+UNIT = "MLUPS"
+SHAPE = (256, 256, 256)
+WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.5Tc, Maxwell coexistence densities, "
+            "random sphere droplets r~U[10,40] (seed 2306, liquid fraction>=0.10), kappa=0.5, sigma=0.1, "
+            "G=-1, default rates, FP32 populations (AA in place)")
+
+
+def algorithmic_bytes(Q):
+    """Bytes per cell update that the method must move: collide-stream reads and writes the Q
+    populations and reads psi once (8Q + 4); the density/psi pass reads the Q populations and
+    writes psi (4Q + 4)."""
+    return {"collide": 8 * Q + 4, "psi": 4 * Q + 4, "step": 12 * Q + 8}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_fields(shape, scale=1.0):
+    c = W.constants()["cs"]
+    t = c["T0.5"]
+    rho, u, spheres = W.random_spheres(shape, t["rho_l"], t["rho_v"], 10.0 * scale, 40.0 * scale, seed=2306,
+                                       target_fraction=0.10, gap=4.0 * max(scale, 0.5))
+    params = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.5)
+    return rho, u, params
+
+
+# ---------------------------------------------------------------- clocks sampling
+class Clocks:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for (t, line) in self.lines:
+            if self.t0 is not None and not (self.t0 - 0.05 <= t <= (self.t1 or t) + 0.15):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, local):
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- our arm
+def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None):
+    import torch
+
+    from paper_2306_16274_gb300 import Params, Simulation
+    p = Params(lattice=Q, shape=SHAPE, **wparams)
+    stream = torch.cuda.Stream()
+    sim = Simulation(p, stream=stream)
+    with torch.cuda.stream(stream):
+        sim.init_fields(torch.tensor(rho, dtype=torch.float32, device="cuda"),
+                        torch.tensor(u, dtype=torch.float32, device="cuda"))
+        sim.step(warmup)
+        sim.sync()
+        _, _, sums0 = sim.moments()
+        sim.set_kernel_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(dist)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark(0)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark(1)
+        barrier(dist)
+        ms = e0.elapsed_time(e1)
+        kms, klaunch = sim.kernel_timing()
+        sim.set_kernel_timing(False)
+        sim.sync()
+        _, _, sums1 = sim.moments()
+    n = float(np.prod(SHAPE))
+    out = dict(ms=ms, kernel_ms=kms, kernel_launches=klaunch, mass_drift=float(abs(sums1[0] - sums0[0]) / sums0[0]),
+               device_bytes=sim.device_bytes)
+    sim.close()
+    del sim
+    torch.cuda.synchronize()
+    out["mlups_local"] = n * steps / (ms * 1e-3) / 1e6
+    return out
+
+
+def run_e2e(Q, rho, u, wparams, steps):
+    """Same metric through the public API with host buffers: pinned host -> device fields,
+    `steps` steps, device -> host moments and sums, timed by the host clock around the whole job."""
+    import torch
+
+    from paper_2306_16274_gb300 import Params, Simulation
+    n = int(np.prod(SHAPE))
+    rho_h = torch.tensor(rho, dtype=torch.float32).pin_memory()
+    u_h = torch.tensor(u, dtype=torch.float32).pin_memory()
+    rho_o = torch.empty(n, dtype=torch.float32).pin_memory()
+    u_o = torch.empty(3 * n, dtype=torch.float32).pin_memory()
+    stream = torch.cuda.Stream()
+    sim = Simulation(Params(lattice=Q, shape=SHAPE, **wparams), stream=stream)
+    import ctypes
+    sums = (ctypes.c_double * 4)()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init_fields(rho_h, u_h)
+    sim.step(steps)
+    sim.moments_into(rho_o, u_o, sums)
+    t1 = time.perf_counter()
+    sim.close()
+    h2d = 4 * n * 4
+    d2h = 4 * n * 4 + 4 * 8
+    return dict(value=n * steps / (t1 - t0) / 1e6, unit=UNIT, h2d_bytes_per_step=h2d / steps,
+                d2h_bytes_per_step=d2h / steps, seconds=t1 - t0)
+
+
+# ---------------------------------------------------------------- oracle timing on host cores
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import bench, workloads as W
+from oracle import lbm
+shape = {shape!r}
+rho, u, wp = bench.workload_fields(shape, scale={scale!r})
+rates = dict(lbm._mom.DEFAULT_RATES)
+p = lbm.Params(lattice={Q}, shape=shape, eos="cs", eos_p=tuple(wp["eos_p"]), G=-1.0, sigma=0.1, kappa=0.5,
+               rates=rates)
+s = lbm.State.from_fields(p, rho, u)
+s.step()
+steps, t0 = 0, time.perf_counter()
+times = []
+while True:
+    a = time.perf_counter(); s.step(); times.append(time.perf_counter() - a); steps += 1
+    if time.perf_counter() - t0 > {budget!r} or steps >= {max_steps}:
+        break
+el = time.perf_counter() - t0
+n = shape[0] * shape[1] * shape[2]
+print(json.dumps(dict(steps=steps, seconds=el, mlups=n * steps / el / 1e6, step_times=times)))
+"""
+
+
+def oracle_timing(Q, budget, max_steps=10 ** 9, shape=(64, 64, 64)):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    code = ORACLE_SNIPPET.format(root=ROOT, shape=shape, scale=shape[0] / SHAPE[0], Q=Q, budget=budget,
+                                 max_steps=max_steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=budget + 600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    Q = 19
+    shape = (64, 64, 64)
+    w = oracle_timing(Q, budget=1e9, max_steps=args.warmup, shape=shape) if args.warmup > 0 else None
+    r = oracle_timing(Q, budget=1e9, max_steps=args.steps, shape=shape)
+    value = r["mlups"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / r["steps"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " -- oracle sample: 64^3 copy (radii scaled 1/4), one step per step",
+                       "lattice": Q, "shape": list(shape)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{shape[0]}^3 copy of the workload, {r['steps']} oracle steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- traffic from the committed ncu summary
+def committed_traffic(Q):
+    """dram bytes per launch of the collide kernel from profiles/collide_q{Q}_traffic.json, if present
+    and recorded for the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"collide_q{Q}_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    try:
+        import hashlib
+        src = open(os.path.join(ROOT, "paper_2306_16274_gb300", "csrc", "kernels_impl.cuh"), "rb").read()
+        src += open(os.path.join(ROOT, "paper_2306_16274_gb300", "csrc", "lbm_device.cuh"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != d.get("kernel_source_sha256_16"):
+            return None
+        cells_full = float(np.prod(SHAPE))
+        return d["dram_bytes_per_launch"] * cells_full / d["cells"]
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-q27", action="store_true")
+    ap.add_argument("--size", type=int, default=256,
+                    help="cubic edge; anything but 256 is a profiling case, not the benchmark workload")
+    args = ap.parse_args()
+    global SHAPE
+    if args.size != 256:
+        SHAPE = (args.size,) * 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, ws, rank)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    dist = init_dist(ws, local)
+    torch.cuda.set_device(local)
+    rho, u, wparams = workload_fields(SHAPE, scale=SHAPE[0] / 256.0)
+    n = float(np.prod(SHAPE))
+    peak, peak_kind = measured_peaks()
+
+    clocks = Clocks(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    r19 = run_lattice(19, rho, u, wparams, args.steps, args.warmup, dist, clocks)
+    clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(dist, r19["ms"])
+    value = ws * n * args.steps / (ms * 1e-3) / 1e6
+    r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
+    e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
+    if rank != 0:
+        return
+    ab = algorithmic_bytes(19)
+    coll_ms = r19["kernel_ms"]["collide"] / max(r19["kernel_launches"]["collide"], 1)
+    psi_ms = r19["kernel_ms"]["psi"] / max(r19["kernel_launches"]["psi"], 1)
+    achieved = ab["collide"] * n / (coll_ms * 1e-3) / 1e9
+    traffic = committed_traffic(19)
+    step_gbs = ab["step"] * n * args.steps / (r19["ms"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if SHAPE == (256, 256, 256) else f"PROFILING CASE {SHAPE}",
+                   "lattice": 19, "shape": list(SHAPE), "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (populations %.2f GB per domain)" % (19 * 4 * n / 1e9)},
+        "hbm_frac_step": step_gbs / peak,
+        "roofline": {"kernel": "collide_kernel (fused collide-stream, D3Q19)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_cell": ab["collide"], "avg_launch_ms": coll_ms},
+        "kernels": {"collide": {"avg_ms": coll_ms, "launches": r19["kernel_launches"]["collide"],
+                                "gbs": achieved},
+                    "psi": {"avg_ms": psi_ms, "launches": r19["kernel_launches"]["psi"],
+                            "gbs": ab["psi"] * n / (psi_ms * 1e-3) / 1e9 if psi_ms > 0 else None}},
+        "gpu_launches": int(r19["kernel_launches"]["collide"] + r19["kernel_launches"]["psi"]),
+        "mass_drift_rel": r19["mass_drift"],
+        "clocks": clk,
+    }
+    if r27:
+        ab27 = algorithmic_bytes(27)
+        c27 = r27["kernel_ms"]["collide"] / max(r27["kernel_launches"]["collide"], 1)
+        line["d3q27"] = {"value": r27["mlups_local"], "unit": UNIT, "ms_per_step": r27["ms"] / args.steps,
+                         "hbm_frac_step": ab27["step"] * n * args.steps / (r27["ms"] * 1e-3) / 1e9 / peak,
+                         "collide_gbs": ab27["collide"] * n / (c27 * 1e-3) / 1e9, "mass_drift_rel": r27["mass_drift"]}
+    if e2e:
+        line["e2e"] = e2e
+    if ws == 1 and not args.no_cpu_baseline:
+        try:
+            cb = oracle_timing(19, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": cb["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"64^3 copy of the workload (radii scaled 1/4), {cb['steps']} FP64 "
+                                              f"oracle steps in {cb['seconds']:.1f} s, one thread"}
+        except Exception as exc:  # the baseline is context; never lose the GPU line over it
+            line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

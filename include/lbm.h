@@ -1,0 +1,183 @@
+/*
+ * lbm.h -- C ABI of liblbm.so: the fused per-time-step update of the
+ * non-orthogonal multiple-relaxation-time (MRT) lattice Boltzmann method with
+ * the square-root pseudopotential multiphase model, on D3Q19 and D3Q27, for
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Fei, Du, Luo, Succi, Lauricella, Montessori, Wang, "Modeling
+ * realistic multiphase flows using a non-orthogonal multiple-relaxation-time
+ * lattice Boltzmann method" (arXiv:2306.16274).  One call of lbm_step(ctx, 1)
+ * performs, for every fluid cell x:
+ *   - pull of the shifted populations f_bar_i (streaming, Eq. e9, kept in place
+ *     with the AA access pattern), density rho = sum_i f_bar_i (Sec. II A);
+ *   - the interaction force F_int (Eq. e15) from the square-root pseudopotential
+ *     psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. II C), the wetting force F_ads
+ *     (Sec. III E), the surface-tension tensor Q (Eq. e18) and a body force;
+ *   - velocity u = (sum_i f_bar_i e_i + F/2) / rho (Sec. II A);
+ *   - m_bar = M f_bar with the non-orthogonal M of Eq. e11 / Eq. "matrix",
+ *     relaxation m_bar* = m_bar - S (m_bar - m^eq) + (I - S/2) F~' (Eq. e8) with
+ *     m^eq of Eq. e13 and F~ of Eq. e14 modified by Eq. e17;
+ *   - f_bar* = M^-1 m_bar* and the store (Eq. e9), with half-way bounce-back at
+ *     solid links;
+ * then recomputes rho and psi for the next step.
+ *
+ * Conventions for every entry point
+ *   - Fields are structure-of-arrays, x fastest: index (z * ny + y) * nx + x.
+ *     A velocity field is three such planes (u_x, u_y, u_z) back to back.
+ *     Populations are Q such planes in the velocity order of Eq. e1.
+ *   - `ptrs_on_device` != 0 means every array argument of that call is CUDA
+ *     device memory of the current device; 0 means host memory.  Host copies
+ *     go through the context's stream and the call synchronises that stream.
+ *   - The library owns all device state of a context; callers own every buffer
+ *     they pass in.  No allocation crosses the ABI.
+ *   - Work is enqueued on the CUDA stream given to lbm_create (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream).
+ *   - Errors are returned as lbm_status; lbm_last_error(ctx) gives a message.
+ *     Nothing throws, exits or traps.  LBM_ERR_UNSTABLE and LBM_ERR_EOS_RANGE
+ *     are sticky: further lbm_step calls return them until lbm_init_fields or
+ *     lbm_set_populations resets the state.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,        /* invalid argument or parameter set                        */
+    LBM_ERR_OOM = 2,        /* a device allocation failed                               */
+    LBM_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed              */
+    LBM_ERR_UNSTABLE = 4,   /* NaN / Inf / non-positive density seen on a fluid cell    */
+    LBM_ERR_EOS_RANGE = 5,  /* psi^2 < 0 on some cell: density outside the EOS range;   */
+                            /* psi was clamped to 0 there                               */
+    LBM_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up                       */
+    LBM_ERR_STATE = 7       /* call out of order (e.g. lbm_step before lbm_init_fields) */
+} lbm_status;
+
+/* equation of state for psi (Sec. II C, Sec. III A) */
+enum {
+    LBM_EOS_NONE = 0,       /* single phase: no pseudopotential, F = rho g                */
+    LBM_EOS_CS = 1,         /* Carnahan-Starling: eos_p = {a, b, R, T}                     */
+    LBM_EOS_PIECEWISE = 2   /* piecewise linear, Eq. e19: eos_p = {rho1, rho2, theta_v,   */
+                            /*   theta_m, theta_l}                                        */
+};
+
+/* per-axis boundary */
+enum {
+    LBM_BC_PERIODIC = 0,
+    LBM_BC_WALL = 1         /* no-slip walls half-way outside the first and last planes   */
+                            /* (half-way bounce-back, Sec. IV A / IV B "non-slip")         */
+};
+
+typedef struct {
+    int32_t lattice;        /* 19 (App. C) or 27 (Sec. II)                                   */
+    int32_t nx, ny, nz;     /* cells per axis, each >= 1                                     */
+    int32_t bc[3];          /* LBM_BC_* for x, y, z                                          */
+    int32_t eos;            /* LBM_EOS_*                                                     */
+    double eos_p[5];        /* EOS parameters, see above                                     */
+    double G;               /* interaction strength of Eq. e15 (Sec. III A uses -1)          */
+    double G_ads;           /* fluid-solid strength of F_ads (Sec. III E); 0 = neutral wall  */
+    double kappa;           /* surface-tension tuning of Eq. e18                             */
+    double sigma;           /* mechanical-stability parameter of Eq. e17                     */
+    double s[10];           /* relaxation rates s0, s1, s2, s2b, s3, s3b, s4, s4b, s5, s6    */
+                            /* of Eq. e12, each in (0, 2)                                    */
+    int32_t variable_nu;    /* 1: nu(rho) = nu_v + (nu_l - nu_v)(rho - rho_v)/(rho_l - rho_v) */
+    double nu_l, nu_v;      /* (Sec. IV A) replaces s2 per cell; 0: s2 is used everywhere    */
+    double rho_l, rho_v;
+    double g[3];            /* body force per unit mass (F includes rho g)                   */
+    double psi_fp64_rho;    /* C-S only: cells with rho >= this evaluate p_EOS - rho c_s^2   */
+                            /* in FP64 (liquid branch); a negative value selects the default */
+                            /* b * rho_c = 0.52177 (critical density); +inf: never           */
+} lbm_params;
+
+/* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,
+ * s0 = s1 = 1, s2b = s3b = 0.6, others 1.2 (text after Eq. e12), sigma = 0.1
+ * (Sec. III A), everything else 0, psi_fp64_rho = -1 (default threshold). */
+void lbm_default_params(lbm_params* p);
+
+/* Validates *params, allocates the device state on the current device and
+ * binds the context to `cuda_stream`.  *out receives the context, or NULL on
+ * error.  Errors: LBM_ERR_ARG (bad lattice, sizes, rates outside (0,2),
+ * G == 0 with an EOS, ...), LBM_ERR_OOM, LBM_ERR_CUDA.  The message of a
+ * failed create is returned by lbm_last_error(NULL). */
+lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out);
+
+/* Sets f_bar(t = 0) = M^-1 m^eq(rho, u) (Eq. e13) on every fluid cell and
+ * computes psi.  rho: N floats; u: 3 N floats (u_x, u_y, u_z planes); solid:
+ * N bytes (nonzero = solid cell) or NULL for none.  Solid cells carry no
+ * populations and report rho = u = 0.  Resets the step counter and any sticky
+ * error.  The solid mask may only be passed on the first call or unchanged in
+ * "has solid" status (a context created without solids that later gets a mask
+ * is accepted; the mask is copied). */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const float* rho, const float* u, const uint8_t* solid,
+                           int ptrs_on_device);
+
+/* Enqueues n >= 0 time steps on the context's stream and returns without
+ * waiting.  Returns a sticky error recorded by an earlier lbm_sync. */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
+
+/* Waits for the context's stream and reads the device status word:
+ * LBM_ERR_UNSTABLE (NaN/Inf or rho <= 0 seen) or LBM_ERR_EOS_RANGE (psi^2 < 0
+ * seen) become sticky. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* rho (N floats) and u = (sum f e + F/2)/rho (3 N floats) of the current state
+ * (Sec. II A).  Either pointer may be NULL.  sums (4 doubles, host, may be
+ * NULL) receives the FP64 totals over fluid cells: sum rho, sum rho u_x,
+ * sum rho u_y, sum rho u_z, reduced in a fixed order (deterministic).
+ * Synchronises the stream and returns the status as lbm_sync does. */
+lbm_status lbm_get_moments(lbm_ctx* ctx, float* rho, float* u, double* sums, int ptrs_on_device);
+
+/* psi (Sec. II C) of the current state, N floats (0 on solid cells). */
+lbm_status lbm_get_psi(lbm_ctx* ctx, float* psi, int ptrs_on_device);
+
+/* Checkpoint: the populations of the current state in natural order
+ * (f_bar_i(x, t) in plane i), Q N floats, whatever the internal AA phase. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, float* f, int ptrs_on_device);
+
+/* Restore: sets the populations (Q N floats, natural order), recomputes psi,
+ * clears sticky errors.  The step counter is kept. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const float* f, int ptrs_on_device);
+
+/* Rebinds the context to another stream (after the caller ordered the two). */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Kernel timing: when enabled, lbm_step records CUDA events on the context's
+ * stream between its kernel launches.  lbm_get_kernel_timing synchronises and
+ * returns the accumulated milliseconds and launch counts of the two step
+ * kernels since the last reset: [0] = density/psi pass, [1] = fused
+ * collide-stream pass.  Enabling resets the counters. */
+lbm_status lbm_set_kernel_timing(lbm_ctx* ctx, int enable);
+lbm_status lbm_get_kernel_timing(lbm_ctx* ctx, double ms[2], int64_t launches[2]);
+
+/* Number of steps taken since lbm_init_fields (or -1 for a NULL context). */
+int64_t lbm_step_count(const lbm_ctx* ctx);
+
+/* Total device bytes the context holds. */
+size_t lbm_device_bytes(const lbm_ctx* ctx);
+
+/* Frees the device state.  Waits for the stream first.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last error on ctx (ctx == NULL: the last failed lbm_create
+ * on this thread).  Never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Name of a status code. */
+const char* lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

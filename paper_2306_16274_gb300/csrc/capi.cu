@@ -1,0 +1,542 @@
+// C ABI of liblbm.so (declared in include/lbm.h): context lifetime, parameter
+// validation and derivation, step sequencing (AA parity), host<->device
+// marshalling, status handling and kernel timing.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::KParams;
+
+struct lbm_ctx {
+    lbm_params p{};
+    int Q = 19;
+    KParams kp{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // device state
+    float* f = nullptr;          // Q planes of `plane` floats (AA layout)
+    float* psi = nullptr;        // ncell floats
+    uint32_t* nbmask = nullptr;  // ncell words, only when a solid mask was given
+    unsigned* status = nullptr;  // device status word
+    double* partials = nullptr;  // moments partial sums (4 per block)
+    double* sums = nullptr;      // 4 doubles
+    float* staging = nullptr;    // ncell * max(Q, 4) floats for host transfers
+    uint8_t* solid_dev = nullptr;
+    size_t bytes = 0;
+    long long partial_blocks = 0;
+    // host state
+    int parity = 0;              // 0: natural layout, 1: swapped (after an odd number of AA steps)
+    long long t = 0;
+    bool initialised = false;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double ms[2] = {0.0, 0.0};
+    long long launches[2] = {0, 0};
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define CK(ctx, call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+bool rate_ok(double s) { return s > 0.0 && s < 2.0 && std::isfinite(s); }
+
+lbm_status validate(const lbm_params* p, std::string& why) {
+    if (!p) { why = "params is NULL"; return LBM_ERR_ARG; }
+    if (p->lattice != 19 && p->lattice != 27) { why = "lattice must be 19 or 27"; return LBM_ERR_ARG; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_ERR_ARG; }
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n > (1LL << 40)) { why = "domain too large"; return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (p->bc[a] != LBM_BC_PERIODIC && p->bc[a] != LBM_BC_WALL) { why = "bc must be 0 or 1"; return LBM_ERR_ARG; }
+    for (int k = 0; k < 10; ++k)
+        if (!rate_ok(p->s[k])) { why = "relaxation rates must lie in (0, 2)"; return LBM_ERR_ARG; }
+    if (p->eos != LBM_EOS_NONE && p->eos != LBM_EOS_CS && p->eos != LBM_EOS_PIECEWISE) {
+        why = "unknown eos";
+        return LBM_ERR_ARG;
+    }
+    if (p->eos != LBM_EOS_NONE) {
+        if (!(p->G != 0.0) || !std::isfinite(p->G)) { why = "a multiphase EOS needs a finite G != 0"; return LBM_ERR_ARG; }
+        if (p->eos == LBM_EOS_CS && !(p->eos_p[1] > 0.0 && p->eos_p[2] > 0.0 && p->eos_p[3] > 0.0)) {
+            why = "Carnahan-Starling needs b, R, T > 0";
+            return LBM_ERR_ARG;
+        }
+        if (p->eos == LBM_EOS_PIECEWISE && !(p->eos_p[0] > 0.0 && p->eos_p[1] > p->eos_p[0])) {
+            why = "piecewise EOS needs 0 < rho1 < rho2";
+            return LBM_ERR_ARG;
+        }
+    }
+    if (p->variable_nu) {
+        if (!(p->rho_l != p->rho_v) || !(p->nu_l > 0.0) || !(p->nu_v > 0.0)) {
+            why = "variable viscosity needs rho_l != rho_v and nu_l, nu_v > 0";
+            return LBM_ERR_ARG;
+        }
+    }
+    return LBM_OK;
+}
+
+KParams derive(const lbm_params& p, long long plane) {
+    KParams k{};
+    k.nx = p.nx;
+    k.ny = p.ny;
+    k.nz = p.nz;
+    k.wall_x = p.bc[0] == LBM_BC_WALL;
+    k.wall_y = p.bc[1] == LBM_BC_WALL;
+    k.wall_z = p.bc[2] == LBM_BC_WALL;
+    k.ncell = (long long)p.nx * p.ny * p.nz;
+    k.plane = plane;
+    k.multiphase = p.eos != LBM_EOS_NONE;
+    k.eos = p.eos;
+    if (p.eos == LBM_EOS_CS) {
+        const double a = p.eos_p[0], b = p.eos_p[1], R = p.eos_p[2], T = p.eos_p[3];
+        k.cs_a_d = a;
+        k.cs_b4_d = b / 4.0;
+        k.cs_RT_d = R * T;
+        k.cs_a = (float)a;
+        k.cs_b4 = (float)(b / 4.0);
+        k.cs_RT = (float)(R * T);
+        // default FP64 threshold: the critical density b rho_c = 0.52177 of the C-S fluid
+        const double thr = p.psi_fp64_rho < 0.0 ? 0.52177 / b : p.psi_fp64_rho;
+        k.psi_fp64_rho = (float)thr;
+    } else {
+        k.psi_fp64_rho = INFINITY;
+    }
+    if (p.eos == LBM_EOS_PIECEWISE) {
+        k.pw_rho1 = (float)p.eos_p[0];
+        k.pw_rho2 = (float)p.eos_p[1];
+        k.pw_tv = (float)p.eos_p[2];
+        k.pw_tm = (float)p.eos_p[3];
+        k.pw_tl = (float)p.eos_p[4];
+        const double p1 = p.eos_p[0] * p.eos_p[2];
+        k.pw_p1 = (float)p1;
+        k.pw_p2 = (float)(p1 + (p.eos_p[1] - p.eos_p[0]) * p.eos_p[3]);
+    }
+    const double G = k.multiphase ? p.G : 0.0;
+    k.G = (float)G;
+    k.G_ads = k.multiphase ? (float)p.G_ads : 0.0f;
+    k.two_over_G_d = G != 0.0 ? 2.0 / G : 0.0;
+    k.two_over_G = (float)k.two_over_G_d;
+    k.kappa_G_half = (float)(p.kappa * G / 2.0);
+    const double t_e = 1.0 / p.s[3] - 0.5;    // s_e = s2b (rate of m_7)
+    k.sigma_coef = (float)(k.multiphase ? 6.0 * p.sigma * G * G / t_e : 0.0);
+    k.q7_coef = (float)(4.0 / (5.0 * t_e));
+    for (int i = 0; i < 10; ++i) {
+        k.s[i] = (float)p.s[i];
+        k.c[i] = (float)(1.0 - 0.5 * p.s[i]);
+    }
+    k.inv_tnu = (float)(1.0 / (1.0 / p.s[2] - 0.5));
+    k.variable_nu = p.variable_nu ? 1 : 0;
+    if (p.variable_nu) {
+        k.nu_v = (float)p.nu_v;
+        k.rho_v = (float)p.rho_v;
+        k.dnu_drho = (float)((p.nu_l - p.nu_v) / (p.rho_l - p.rho_v));
+    }
+    k.gx = (float)p.g[0];
+    k.gy = (float)p.g[1];
+    k.gz = (float)p.g[2];
+    return k;
+}
+
+bool has_solids(const lbm_ctx* c) {
+    return c->nbmask != nullptr || c->kp.wall_x || c->kp.wall_y || c->kp.wall_z;
+}
+
+cudaError_t run_psi(lbm_ctx* c) {
+    if (!c->kp.multiphase) return cudaSuccess;
+    const int s = has_solids(c);
+    return c->Q == 19 ? lbm::launch_psi_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream)
+                      : lbm::launch_psi_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream);
+}
+
+cudaError_t run_collide(lbm_ctx* c) {
+    const int s = has_solids(c);
+    return c->Q == 19 ? lbm::launch_collide_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream)
+                      : lbm::launch_collide_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream);
+}
+
+cudaError_t record(lbm_ctx* c) {
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        c->ev.push_back(e);
+    }
+    return cudaEventRecord(c->ev[c->ev_used++], c->stream);
+}
+
+// Accumulates the event intervals recorded so far: events come as
+// [e0 psi e1 collide e2] per step.
+cudaError_t drain_timing(lbm_ctx* c) {
+    if (c->ev_used == 0) return cudaSuccess;
+    cudaError_t e = cudaEventSynchronize(c->ev[c->ev_used - 1]);
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k + 2 < c->ev_used; k += 3) {
+        float a = 0.f, b = 0.f;
+        if ((e = cudaEventElapsedTime(&a, c->ev[k], c->ev[k + 1])) != cudaSuccess) return e;
+        if ((e = cudaEventElapsedTime(&b, c->ev[k + 1], c->ev[k + 2])) != cudaSuccess) return e;
+        c->ms[1] += a;   // collide runs first in a step
+        c->ms[0] += b;
+        c->launches[1] += 1;
+        if (c->kp.multiphase) c->launches[0] += 1;
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+
+lbm_status read_status(lbm_ctx* c) {
+    unsigned st = 0;
+    CK(c, cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (c->sticky == LBM_OK) {
+        if (st & lbm::ST_UNSTABLE) {
+            c->sticky = LBM_ERR_UNSTABLE;
+            c->err = "non-finite or non-positive density on a fluid cell";
+        } else if (st & lbm::ST_EOS_RANGE) {
+            c->sticky = LBM_ERR_EOS_RANGE;
+            c->err = "psi^2 < 0: density outside the range of the equation of state (psi clamped to 0)";
+        }
+    }
+    return c->sticky;
+}
+
+// copy helper: device destination or host destination through the stream
+lbm_status copy_out(lbm_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+    CK(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->lattice = 19;
+    p->nx = p->ny = p->nz = 32;
+    p->eos = LBM_EOS_NONE;
+    p->G = -1.0;
+    p->sigma = 0.1;
+    const double s[10] = {1.0, 1.0, 1.2, 0.6, 1.2, 0.6, 1.2, 1.2, 1.2, 1.2};
+    for (int i = 0; i < 10; ++i) p->s[i] = s[i];
+    p->psi_fp64_rho = -1.0;
+}
+
+lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    lbm_status v = validate(params, why);
+    if (v != LBM_OK) return fail(nullptr, v, why);
+    lbm_ctx* c = new lbm_ctx();
+    c->p = *params;
+    c->Q = params->lattice;
+    c->stream = (cudaStream_t)cuda_stream;
+    const long long n = (long long)params->nx * params->ny * params->nz;
+    const long long plane = (n + 63) / 64 * 64;   // 256-byte aligned planes
+    c->kp = derive(*params, plane);
+    c->partial_blocks = lbm::moments_partial_blocks(c->kp);
+    auto alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e == cudaSuccess) c->bytes += bytes;
+        return e;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    const int stage_w = c->Q > 4 ? c->Q : 4;
+    if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * sizeof(float));
+    if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
+    if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
+    if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
+    if (e == cudaSuccess) e = alloc((void**)&c->sums, 4 * sizeof(double));
+    if (e == cudaSuccess) e = alloc((void**)&c->staging, (size_t)stage_w * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 64, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->psi, 0, (size_t)n * sizeof(float), c->stream);
+    if (e != cudaSuccess) {
+        lbm_status s = e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+        std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        (void)cudaGetLastError();
+        lbm_destroy(c);
+        return fail(nullptr, s, msg);
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const uint8_t* solid, int on_device) {
+    if (!c) return LBM_ERR_ARG;
+    if (!rho || !u) return fail(c, LBM_ERR_ARG, "rho and u are required");
+    const long long n = c->kp.ncell;
+    const float* d_rho = rho;
+    const float* d_u = u;
+    if (!on_device) {
+        CK(c, cudaMemcpyAsync(c->staging, rho, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->staging + n, u, 3 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        d_rho = c->staging;
+        d_u = c->staging + n;
+    }
+    if (solid) {
+        if (!c->nbmask) {
+            CK(c, cudaMalloc((void**)&c->nbmask, n * sizeof(uint32_t)));
+            c->bytes += n * sizeof(uint32_t);
+        }
+        if (!c->solid_dev) {
+            CK(c, cudaMalloc((void**)&c->solid_dev, n));
+            c->bytes += n;
+        }
+        CK(c, cudaMemcpyAsync(c->solid_dev, solid, n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+        CK(c, lbm::launch_nbmask(c->kp, c->Q, c->solid_dev, c->nbmask, c->stream));
+    } else if (c->nbmask) {
+        // walls are handled arithmetically; no mask means "no interior solids"
+        CK(c, cudaFree(c->nbmask));
+        c->bytes -= n * sizeof(uint32_t);
+        c->nbmask = nullptr;
+    }
+    CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream)
+                     : lbm::launch_init_q27(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream));
+    c->parity = 0;
+    c->t = 0;
+    c->sticky = LBM_OK;
+    CK(c, cudaMemsetAsync(c->status, 0, 64, c->stream));
+    CK(c, run_psi(c));
+    c->initialised = true;
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int32_t n) {
+    if (!c) return LBM_ERR_ARG;
+    if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
+    if (c->sticky != LBM_OK) return c->sticky;
+    for (int32_t k = 0; k < n; ++k) {
+        // psi of the current state is valid on entry: collide-stream, then density/psi of the new state
+        if (c->timing) CK(c, record(c));
+        CK(c, run_collide(c));
+        c->parity ^= 1;
+        if (c->timing) CK(c, record(c));
+        CK(c, run_psi(c));
+        if (c->timing) CK(c, record(c));
+        c->t += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    return read_status(c);
+}
+
+lbm_status lbm_get_moments(lbm_ctx* c, float* rho, float* u, double* sums, int on_device) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_moments before lbm_init_fields");
+    const long long n = c->kp.ncell;
+    float* d_rho = on_device ? rho : (rho ? c->staging : nullptr);
+    float* d_u = on_device ? u : (u ? c->staging + n : nullptr);
+    int nb = 0;
+    const int s = has_solids(c);
+    CK(c, c->Q == 19 ? lbm::launch_moments_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, d_rho, d_u, c->partials,
+                                               &nb, c->stream)
+                     : lbm::launch_moments_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, d_rho, d_u, c->partials,
+                                               &nb, c->stream));
+    CK(c, lbm::launch_finish_sums(c->partials, nb, c->sums, c->stream));
+    if (!on_device) {
+        if (rho) CK(c, cudaMemcpyAsync(rho, d_rho, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        if (u) CK(c, cudaMemcpyAsync(u, d_u, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (sums) CK(c, cudaMemcpyAsync(sums, c->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+}
+
+lbm_status lbm_get_psi(lbm_ctx* c, float* psi, int on_device) {
+    if (!c || !psi) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_psi before lbm_init_fields");
+    lbm_status s = copy_out(c, psi, c->psi, c->kp.ncell * sizeof(float), on_device);
+    if (s != LBM_OK) return s;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, float* f, int on_device) {
+    if (!c || !f) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_populations before lbm_init_fields");
+    const long long n = c->kp.ncell;
+    float* dst = on_device ? f : c->staging;
+    const int s = has_solids(c);
+    CK(c, c->Q == 19 ? lbm::launch_gather_q19(c->kp, c->parity, s, c->f, c->nbmask, dst, c->stream)
+                     : lbm::launch_gather_q27(c->kp, c->parity, s, c->f, c->nbmask, dst, c->stream));
+    if (!on_device) CK(c, cudaMemcpyAsync(f, dst, (size_t)c->Q * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const float* f, int on_device) {
+    if (!c || !f) return LBM_ERR_ARG;
+    const long long n = c->kp.ncell;
+    CK(c, cudaMemcpy2DAsync(c->f, c->kp.plane * sizeof(float), f, n * sizeof(float), n * sizeof(float), c->Q,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->parity = 0;
+    c->sticky = LBM_OK;
+    CK(c, cudaMemsetAsync(c->status, 0, 64, c->stream));
+    CK(c, run_psi(c));
+    c->initialised = true;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
+    if (!c) return LBM_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_kernel_timing(lbm_ctx* c, int enable) {
+    if (!c) return LBM_ERR_ARG;
+    CK(c, drain_timing(c));
+    c->timing = enable != 0;
+    c->ms[0] = c->ms[1] = 0.0;
+    c->launches[0] = c->launches[1] = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_timing(lbm_ctx* c, double ms[2], int64_t launches[2]) {
+    if (!c) return LBM_ERR_ARG;
+    CK(c, drain_timing(c));
+    if (ms) { ms[0] = c->ms[0]; ms[1] = c->ms[1]; }
+    if (launches) { launches[0] = c->launches[0]; launches[1] = c->launches[1]; }
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_ctx* c) { return c ? c->t : -1; }
+
+size_t lbm_device_bytes(const lbm_ctx* c) { return c ? c->bytes : 0; }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->stream || c->f) (void)cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->ev) (void)cudaEventDestroy(e);
+    void* ptrs[] = {c->f, c->psi, c->nbmask, c->status, c->partials, c->sums, c->staging, c->solid_dev};
+    for (void* p : ptrs)
+        if (p) (void)cudaFree(p);
+    delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+const char* lbm_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_ERR_ARG: return "LBM_ERR_ARG";
+        case LBM_ERR_OOM: return "LBM_ERR_OOM";
+        case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+        case LBM_ERR_UNSTABLE: return "LBM_ERR_UNSTABLE";
+        case LBM_ERR_EOS_RANGE: return "LBM_ERR_EOS_RANGE";
+        case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+        case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    }
+    return "LBM_UNKNOWN";
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ lattice-independent kernels
+namespace lbm {
+namespace {
+
+__host__ __device__ constexpr int ex27(int i) {
+    constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int ey27(int i) {
+    constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int ez27(int i) {
+    constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+    return t[i];
+}
+
+// bit i of nbmask[x] <=> x + e_i is an interior solid cell (bit 0: x itself).  Walls are not
+// stored here; the kernels add them from the position.
+__global__ void nbmask_kernel(KParams kp, int Q, const uint8_t* __restrict__ solid, uint32_t* __restrict__ out) {
+    const long long n = kp.ncell;
+    const long long nxy = (long long)kp.nx * kp.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % kp.nx), y = (int)((idx / kp.nx) % kp.ny), z = (int)(idx / nxy);
+        uint32_t bits = 0u;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            if (i >= Q) break;
+            int xx = x + ex27(i), yy = y + ey27(i), zz = z + ez27(i);
+            bool outside = false;
+            if (xx < 0 || xx >= kp.nx) { if (kp.wall_x) outside = true; else xx = (xx + kp.nx) % kp.nx; }
+            if (yy < 0 || yy >= kp.ny) { if (kp.wall_y) outside = true; else yy = (yy + kp.ny) % kp.ny; }
+            if (zz < 0 || zz >= kp.nz) { if (kp.wall_z) outside = true; else zz = (zz + kp.nz) % kp.nz; }
+            if (!outside && solid[zz * nxy + (long long)yy * kp.nx + xx]) bits |= 1u << i;
+        }
+        out[idx] = bits;
+    }
+}
+
+// Sums per-block partials in a fixed order (one block, fixed thread assignment, fixed tree).
+__global__ void finish_sums_kernel(const double* __restrict__ partials, int nblocks, double* __restrict__ sums) {
+    __shared__ double red[4][256];
+    const int t = threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = t; b < nblocks; b += 256)
+        for (int k = 0; k < 4; ++k) acc[k] += partials[4 * (long long)b + k];
+    for (int k = 0; k < 4; ++k) red[k][t] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 4; ++k) red[k][t] += red[k][t + w];
+        __syncthreads();
+    }
+    if (t < 4) sums[t] = red[t][0];
+}
+
+}  // namespace
+
+cudaError_t launch_nbmask(const KParams& kp, int Q, const uint8_t* solid, uint32_t* nbmask, cudaStream_t st) {
+    const long long blocks = (kp.ncell + 255) / 256;
+    nbmask_kernel<<<(int)(blocks < 152LL * 64 ? blocks : 152LL * 64), 256, 0, st>>>(kp, Q, solid, nbmask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums, cudaStream_t st) {
+    finish_sums_kernel<<<1, 256, 0, st>>>(partials, nblocks, sums);
+    return cudaGetLastError();
+}
+
+long long moments_partial_blocks(const KParams& kp) {
+    // matches the collide/moments launch shape (32 x 4 x 2 cells per block)
+    return (long long)((kp.nx + 31) / 32) * ((kp.ny + 3) / 4) * ((kp.nz + 1) / 2);
+}
+
+}  // namespace lbm

@@ -1,0 +1,316 @@
+// Kernels of one lattice; included by kernels_q19.cu / kernels_q27.cu with LBM_Q set.
+#pragma once
+
+#include "lbm_device.cuh"
+
+#ifndef LBM_Q
+#error "define LBM_Q (19 or 27) before including kernels_impl.cuh"
+#endif
+
+namespace lbm {
+namespace {
+
+constexpr int Q = LBM_Q;
+
+// ---- density + psi pass (Sec. II A, Sec. II C): one thread per cell, x fastest
+constexpr int PSI_BX = 32, PSI_BY = 4;
+
+template <int PARITY, bool SOLIDS>
+__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const float* __restrict__ f,
+                                                            float* __restrict__ psi,
+                                                            const uint32_t* __restrict__ nbmask,
+                                                            unsigned* status) {
+    const int x = blockIdx.x * PSI_BX + threadIdx.x;
+    const int y = blockIdx.y * PSI_BY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= kp.nx || y >= kp.ny) return;
+    const Cell c = make_cell(kp, x, y, z);
+    const uint32_t bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+    if (bits & 1u) {
+        psi[c.idx] = 0.0f;
+        return;
+    }
+    float p[Q];
+    gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    float rho = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += p[i];
+    psi[c.idx] = eval_psi(kp, rho, status);
+}
+
+// ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
+constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;
+
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+__global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) collide_kernel(KParams kp, float* __restrict__ f,
+                                                                       const float* __restrict__ psi,
+                                                                       const uint32_t* __restrict__ nbmask,
+                                                                       unsigned* status) {
+    __shared__ PsiTile<CS_BX, CS_BY, CS_BZ> tile;
+    const int x0 = blockIdx.x * CS_BX, y0 = blockIdx.y * CS_BY, z0 = blockIdx.z * CS_BZ;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const int tid = threadIdx.x + CS_BX * (threadIdx.y + CS_BY * threadIdx.z);
+    const bool inside = x < kp.nx && y < kp.ny && z < kp.nz;
+
+    Cell c;
+    uint32_t bits = 0u;
+    float p[Q];
+    bool active = false;
+    if (inside) {
+        c = make_cell(kp, x, y, z);
+        bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+        active = !(bits & 1u);
+        if (active) gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    }
+    if (MULTIPHASE) {
+        tile.load(kp, psi, x0, y0, z0, tid);
+        __syncthreads();
+    }
+    if (!active) return;
+
+    Forces Fo;
+    if (MULTIPHASE) {
+        Fo = stencil_forces<Q, SOLIDS>(kp, tile.at(threadIdx.x, threadIdx.y, threadIdx.z), PsiTile<CS_BX, CS_BY, CS_BZ>::TX,
+                                       PsiTile<CS_BX, CS_BY, CS_BZ>::TX * PsiTile<CS_BX, CS_BY, CS_BZ>::TY, bits);
+    } else {
+        Fo.fx = Fo.fy = Fo.fz = 0.f;
+        Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+        Fo.s2 = 0.f;
+    }
+    float rho, ux, uy, uz;
+    collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+    if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+    store<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+}
+
+// ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
+__global__ void init_kernel(KParams kp, float* __restrict__ f, const float* __restrict__ rho_in,
+                            const float* __restrict__ u_in, const uint32_t* __restrict__ nbmask) {
+    const long long n = kp.ncell;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        float out[Q];
+        const bool solid = nbmask && (__ldg(nbmask + idx) & 1u);
+        if (solid) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[i] = 0.0f;
+        } else {
+            const float rho = rho_in[idx];
+            const float ux = u_in[idx], uy = u_in[n + idx], uz = u_in[2 * n + idx];
+            const float cs2 = 1.0f / 3.0f, cs4 = 1.0f / 9.0f, cs6 = 1.0f / 27.0f;
+            const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+            float m[Q];
+            m[0] = rho;
+            m[1] = rho * ux;
+            m[2] = rho * uy;
+            m[3] = rho * uz;
+            m[4] = rho * ux * uy;
+            m[5] = rho * ux * uz;
+            m[6] = rho * uy * uz;
+            m[7] = rho * (1.0f + uxx + uyy + uzz);
+            m[8] = rho * (uxx - uyy);
+            m[9] = rho * (uxx - uzz);
+            m[10] = cs2 * rho * ux;
+            m[11] = cs2 * rho * ux;
+            m[12] = cs2 * rho * uy;
+            m[13] = cs2 * rho * uz;
+            m[14] = cs2 * rho * uy;
+            m[15] = cs2 * rho * uz;
+            if (Q == 27) m[MP<Q>(16)] = 0.0f;
+            m[MP<Q>(17)] = cs2 * rho * (cs2 + uxx + uyy);
+            m[MP<Q>(18)] = cs2 * rho * (cs2 + uxx + uzz);
+            m[MP<Q>(19)] = cs2 * rho * (cs2 + uyy + uzz);
+            if (Q == 27) {
+                m[MP<Q>(20)] = cs2 * rho * uy * uz;
+                m[MP<Q>(21)] = cs2 * rho * ux * uz;
+                m[MP<Q>(22)] = cs2 * rho * ux * uy;
+                m[MP<Q>(23)] = cs4 * rho * ux;
+                m[MP<Q>(24)] = cs4 * rho * uy;
+                m[MP<Q>(25)] = cs4 * rho * uz;
+                m[MP<Q>(26)] = cs4 * rho * (uxx + uyy + uzz) + cs6 * rho;
+            }
+            to_pops<Q>(m, out);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i * kp.plane + idx] = out[i];
+    }
+}
+
+// ---- macroscopic output: rho, u = (sum f e + F/2)/rho, FP64 block partial sums
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+__global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) moments_kernel(KParams kp, const float* __restrict__ f,
+                                                                       const float* __restrict__ psi,
+                                                                       const uint32_t* __restrict__ nbmask,
+                                                                       float* __restrict__ rho_out,
+                                                                       float* __restrict__ u_out,
+                                                                       double* __restrict__ partials) {
+    __shared__ PsiTile<CS_BX, CS_BY, CS_BZ> tile;
+    __shared__ double red[4][CS_BX * CS_BY * CS_BZ / 32];
+    const int x0 = blockIdx.x * CS_BX, y0 = blockIdx.y * CS_BY, z0 = blockIdx.z * CS_BZ;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const int tid = threadIdx.x + CS_BX * (threadIdx.y + CS_BY * threadIdx.z);
+    const bool inside = x < kp.nx && y < kp.ny && z < kp.nz;
+    Cell c;
+    uint32_t bits = 0u;
+    float p[Q];
+    bool active = false;
+    if (inside) {
+        c = make_cell(kp, x, y, z);
+        bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+        active = !(bits & 1u);
+        if (active) gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    }
+    if (MULTIPHASE) {
+        tile.load(kp, psi, x0, y0, z0, tid);
+        __syncthreads();
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+        Forces Fo;
+        if (MULTIPHASE) {
+            Fo = stencil_forces<Q, SOLIDS>(kp, tile.at(threadIdx.x, threadIdx.y, threadIdx.z),
+                                           PsiTile<CS_BX, CS_BY, CS_BZ>::TX,
+                                           PsiTile<CS_BX, CS_BY, CS_BZ>::TX * PsiTile<CS_BX, CS_BY, CS_BZ>::TY, bits);
+        } else {
+            Fo.fx = Fo.fy = Fo.fz = 0.f;
+        }
+        float m[Q];
+        to_moments<Q>(p, m);
+        const float rho = m[0];
+        const float jx = m[1] + 0.5f * (Fo.fx + rho * kp.gx);
+        const float jy = m[2] + 0.5f * (Fo.fy + rho * kp.gy);
+        const float jz = m[3] + 0.5f * (Fo.fz + rho * kp.gz);
+        const float inv = 1.0f / rho;
+        if (rho_out) rho_out[c.idx] = rho;
+        if (u_out) {
+            u_out[c.idx] = jx * inv;
+            u_out[kp.ncell + c.idx] = jy * inv;
+            u_out[2 * kp.ncell + c.idx] = jz * inv;
+        }
+        acc[0] = rho;
+        acc[1] = jx;
+        acc[2] = jy;
+        acc[3] = jz;
+    } else if (inside) {
+        if (rho_out) rho_out[c.idx] = 0.0f;
+        if (u_out) {
+            u_out[c.idx] = 0.0f;
+            u_out[kp.ncell + c.idx] = 0.0f;
+            u_out[2 * kp.ncell + c.idx] = 0.0f;
+        }
+    }
+    // fixed-order block reduction in FP64: warp tree, then warps in order
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((tid & 31) == 0) red[k][tid >> 5] = v;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double s = 0.0;
+        for (int w = 0; w < CS_BX * CS_BY * CS_BZ / 32; ++w) s += red[tid][w];
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        partials[4 * b + tid] = s;
+    }
+}
+
+// ---- checkpoint gather: populations of the current state in natural order
+template <int PARITY, bool SOLIDS>
+__global__ void gather_kernel(KParams kp, const float* __restrict__ f, const uint32_t* __restrict__ nbmask,
+                              float* __restrict__ out) {
+    const int x = blockIdx.x * PSI_BX + threadIdx.x;
+    const int y = blockIdx.y * PSI_BY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= kp.nx || y >= kp.ny) return;
+    const Cell c = make_cell(kp, x, y, z);
+    const uint32_t bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+    float p[Q];
+    if (bits & 1u) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) p[i] = 0.0f;
+    } else {
+        gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i * kp.ncell + c.idx] = p[i];
+}
+
+dim3 psi_grid(const KParams& kp) {
+    return dim3((kp.nx + PSI_BX - 1) / PSI_BX, (kp.ny + PSI_BY - 1) / PSI_BY, kp.nz);
+}
+dim3 cs_grid(const KParams& kp) {
+    return dim3((kp.nx + CS_BX - 1) / CS_BX, (kp.ny + CS_BY - 1) / CS_BY, (kp.nz + CS_BZ - 1) / CS_BZ);
+}
+
+}  // namespace
+
+#define LBM_CAT2(a, b) a##b
+#define LBM_CAT(a, b) LBM_CAT2(a, b)
+
+cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f, float* psi,
+                                         const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
+    const dim3 g = psi_grid(kp), b(PSI_BX, PSI_BY);
+    if (parity == 0 && !solids) psi_kernel<0, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
+    else if (parity == 0) psi_kernel<0, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
+    else if (!solids) psi_kernel<1, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
+    else psi_kernel<1, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, float* f, const float* psi,
+                                             const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
+    const dim3 g = cs_grid(kp), b(CS_BX, CS_BY, CS_BZ);
+    const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
+    switch (key) {
+        case 0: collide_kernel<0, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 1: collide_kernel<0, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 2: collide_kernel<0, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 3: collide_kernel<0, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 4: collide_kernel<1, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 5: collide_kernel<1, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 6: collide_kernel<1, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        default: collide_kernel<1, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, float* f, const float* rho, const float* u,
+                                          const uint32_t* nbmask, cudaStream_t st) {
+    const long long blocks = (kp.ncell + 255) / 256;
+    const int g = (int)(blocks < 152LL * 64 ? blocks : 152LL * 64);
+    init_kernel<<<g, 256, 0, st>>>(kp, f, rho, u, nbmask);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_moments_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f,
+                                             const float* psi, const uint32_t* nbmask, float* rho, float* u,
+                                             double* partials, int* nblocks, cudaStream_t st) {
+    const dim3 g = cs_grid(kp), b(CS_BX, CS_BY, CS_BZ);
+    *nblocks = (int)(g.x * g.y * g.z);
+    const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
+    switch (key) {
+        case 0: moments_kernel<0, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 1: moments_kernel<0, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 2: moments_kernel<0, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 3: moments_kernel<0, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 4: moments_kernel<1, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 5: moments_kernel<1, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        case 6: moments_kernel<1, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+        default: moments_kernel<1, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_gather_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f,
+                                            const uint32_t* nbmask, float* out, cudaStream_t st) {
+    const dim3 g = psi_grid(kp), b(PSI_BX, PSI_BY);
+    if (parity == 0 && !solids) gather_kernel<0, false><<<g, b, 0, st>>>(kp, f, nbmask, out);
+    else if (parity == 0) gather_kernel<0, true><<<g, b, 0, st>>>(kp, f, nbmask, out);
+    else if (!solids) gather_kernel<1, false><<<g, b, 0, st>>>(kp, f, nbmask, out);
+    else gather_kernel<1, true><<<g, b, 0, st>>>(kp, f, nbmask, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

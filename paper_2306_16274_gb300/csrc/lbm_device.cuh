@@ -1,0 +1,331 @@
+// Device code of the fused non-orthogonal MRT pseudopotential step (sm_103a).
+//
+// Data layout: populations are structure-of-arrays, plane i holds f_bar_i for
+// every cell, cell index (z*ny + y)*nx + x (x fastest), planes `plane` floats
+// apart.  Streaming (Eq. e9) is done in place with the AA access pattern:
+//   even step (parity 0): read f_i from slot i of the cell, write the
+//     post-collision f*_i into slot ibar of the same cell;
+//   odd step (parity 1): read f_i from slot ibar of x - e_i, write f*_i into
+//     slot i of x + e_i.
+// Each cell reads and writes the same set of locations, so the update needs no
+// second copy.  Half-way bounce-back: on an odd step a link to a solid
+// neighbour reads/writes the cell's own slot instead (f_i(x) <- slot i of x,
+// f*_i -> slot ibar of x); an even step is local and needs no test.
+#pragma once
+
+#include <stdint.h>
+
+#include "lbm_internal.h"
+#include "transform_q19.cuh"
+#include "transform_q27.cuh"
+
+namespace lbm {
+
+// ------------------------------------------------------------------ lattice (Eq. e1)
+__host__ __device__ constexpr int EX(int i) {
+    constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int EY(int i) {
+    constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int EZ(int i) {
+    constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int OPP(int i) {
+    constexpr int t[27] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15, 26, 25, 24, 23, 22, 21, 20, 19};
+    return t[i];
+}
+// normalised weights w(|e|^2) = omega / c_s^2 of Eq. e15 for the active lattice
+template <int Q>
+__host__ __device__ constexpr float WN(int i) {
+    return (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 1 ? (Q == 27 ? 2.0f / 9.0f : 1.0f / 6.0f)
+         : (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 2 ? (Q == 27 ? 1.0f / 18.0f : 1.0f / 12.0f)
+         : (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 3 ? 1.0f / 72.0f
+         : 0.0f;
+}
+
+template <int Q>
+__device__ __forceinline__ void to_moments(const float (&f)[Q], float (&m)[Q]);
+template <>
+__device__ __forceinline__ void to_moments<19>(const float (&f)[19], float (&m)[19]) { moments_from_pops_q19(f, m); }
+template <>
+__device__ __forceinline__ void to_moments<27>(const float (&f)[27], float (&m)[27]) { moments_from_pops_q27(f, m); }
+template <int Q>
+__device__ __forceinline__ void to_pops(const float (&m)[Q], float (&f)[Q]);
+template <>
+__device__ __forceinline__ void to_pops<19>(const float (&m)[19], float (&f)[19]) { pops_from_moments_q19(m, f); }
+template <>
+__device__ __forceinline__ void to_pops<27>(const float (&m)[27], float (&f)[27]) { pops_from_moments_q27(m, f); }
+
+// position of moment k of Eq. e11 in the lattice's moment vector (App. C keeps 0..15, 17, 18, 19)
+template <int Q>
+__host__ __device__ constexpr int MP(int k) { return (Q == 27 || k < 16) ? k : k - 1; }
+
+// ------------------------------------------------------------------ neighbourhood of a cell
+struct Cell {
+    int x, y, z;
+    long long idx;
+    int xo[3];        // x-1, x, x+1 wrapped (periodic)
+    long long yo[3];  // (y+dy)*nx wrapped
+    long long zo[3];  // (z+dz)*nx*ny wrapped
+    __device__ __forceinline__ long long nb(int dx, int dy, int dz) const {
+        return zo[dz + 1] + yo[dy + 1] + xo[dx + 1];
+    }
+};
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ Cell make_cell(const KParams& kp, int x, int y, int z) {
+    Cell c;
+    c.x = x;
+    c.y = y;
+    c.z = z;
+    const long long nxy = (long long)kp.nx * kp.ny;
+    c.idx = z * nxy + (long long)y * kp.nx + x;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        c.xo[d + 1] = wrap1(x + d, kp.nx);
+        c.yo[d + 1] = (long long)wrap1(y + d, kp.ny) * kp.nx;
+        c.zo[d + 1] = (long long)wrap1(z + d, kp.nz) * nxy;
+    }
+    return c;
+}
+
+// bit i set <=> x + e_i is solid (bit 0: the cell itself).  Walls are the planes
+// just outside the domain on a wall axis; interior solids come from nbmask.
+template <int Q>
+__device__ __forceinline__ uint32_t solid_bits(const KParams& kp, const uint32_t* __restrict__ nbmask, const Cell& c) {
+    uint32_t bits = nbmask ? __ldg(nbmask + c.idx) : 0u;
+    const bool xl = kp.wall_x && c.x == 0, xh = kp.wall_x && c.x == kp.nx - 1;
+    const bool yl = kp.wall_y && c.y == 0, yh = kp.wall_y && c.y == kp.ny - 1;
+    const bool zl = kp.wall_z && c.z == 0, zh = kp.wall_z && c.z == kp.nz - 1;
+    if (xl | xh | yl | yh | zl | zh) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool s = (EX(i) < 0 && xl) || (EX(i) > 0 && xh) || (EY(i) < 0 && yl) || (EY(i) > 0 && yh) ||
+                           (EZ(i) < 0 && zl) || (EZ(i) > 0 && zh);
+            bits |= s ? (1u << i) : 0u;
+        }
+    }
+    return bits;
+}
+
+// ------------------------------------------------------------------ AA gather / store
+template <int Q, int PARITY, bool SOLIDS>
+__device__ __forceinline__ void gather(const KParams& kp, const float* __restrict__ f, const Cell& c, uint32_t bits,
+                                       float (&p)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0) {
+            p[i] = __ldg(f + i * kp.plane + c.idx);
+        } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
+            p[i] = __ldg(f + i * kp.plane + c.idx);   // reflected at the wall in the previous step
+        } else {
+            p[i] = __ldg(f + OPP(i) * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
+        }
+    }
+}
+
+template <int Q, int PARITY, bool SOLIDS>
+__device__ __forceinline__ void store(const KParams& kp, float* __restrict__ f, const Cell& c, uint32_t bits,
+                                      const float (&p)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0) {
+            f[OPP(i) * kp.plane + c.idx] = p[i];
+        } else if (SOLIDS && ((bits >> i) & 1u)) {
+            f[OPP(i) * kp.plane + c.idx] = p[i];       // half-way bounce-back
+        } else {
+            f[i * kp.plane + c.nb(EX(i), EY(i), EZ(i))] = p[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ equation of state -> psi
+// psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. II C).  The Carnahan-Starling
+// liquid branch (rho >= psi_fp64_rho) is evaluated in FP64.
+__device__ __forceinline__ float eval_psi(const KParams& kp, float rho, unsigned* status) {
+    float psi2;
+    if (kp.eos == 1) {
+        if (rho >= kp.psi_fp64_rho) {
+            const double r = rho;
+            const double eta = kp.cs_b4_d * r;
+            const double om = 1.0 - eta;
+            const double p = r * kp.cs_RT_d * (1.0 + eta * (1.0 + eta * (1.0 - eta))) / (om * om * om) -
+                             kp.cs_a_d * r * r;
+            psi2 = (float)(kp.two_over_G_d * (p - r * (1.0 / 3.0)));
+        } else {
+            const float eta = kp.cs_b4 * rho;
+            const float om = 1.0f - eta;
+            const float p = rho * kp.cs_RT * (1.0f + eta * (1.0f + eta * (1.0f - eta))) / (om * om * om) -
+                            kp.cs_a * rho * rho;
+            psi2 = kp.two_over_G * (p - rho * (1.0f / 3.0f));
+        }
+    } else {
+        float p;
+        if (rho <= kp.pw_rho1) p = rho * kp.pw_tv;
+        else if (rho <= kp.pw_rho2) p = kp.pw_p1 + (rho - kp.pw_rho1) * kp.pw_tm;
+        else p = kp.pw_p2 + (rho - kp.pw_rho2) * kp.pw_tl;
+        psi2 = kp.two_over_G * (p - rho * (1.0f / 3.0f));
+    }
+    if (!(psi2 >= 0.0f)) {
+        atomicOr(status, ST_EOS_RANGE);
+        psi2 = 0.0f;
+    }
+    return sqrtf(psi2);
+}
+
+// ------------------------------------------------------------------ psi stencil -> forces
+struct Forces {
+    float fx, fy, fz;        // F_int + F_ads (body force added later)
+    float qxx, qyy, qzz, qxy, qxz, qyz;
+    float s2;                // |S|^2, S = sum_i w_i psi(x + e_i) e_i  (|F_int|^2 / psi^2 = G^2 |S|^2)
+};
+
+// t points at psi(x) inside a tile with x stride 1, y stride sy, z stride sz.
+template <int Q, bool SOLIDS>
+__device__ __forceinline__ Forces stencil_forces(const KParams& kp, const float* t, int sy, int sz, uint32_t bits) {
+    const float pc = t[0];
+    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Ax = 0.f, Ay = 0.f, Az = 0.f;
+    float qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        float pn = t[EX(i) + EY(i) * sy + EZ(i) * sz];
+        if (SOLIDS && ((bits >> i) & 1u)) {
+            pn = pc;   // neutral continuation at a solid neighbour; wetting enters through F_ads only
+            Ax += WN<Q>(i) * EX(i);
+            Ay += WN<Q>(i) * EY(i);
+            Az += WN<Q>(i) * EZ(i);
+        }
+        const float wp = WN<Q>(i) * pn;
+        if (EX(i)) Sx += EX(i) > 0 ? wp : -wp;
+        if (EY(i)) Sy += EY(i) > 0 ? wp : -wp;
+        if (EZ(i)) Sz += EZ(i) > 0 ? wp : -wp;
+        const float wd = WN<Q>(i) * (pn - pc);
+        if (EX(i)) qxx += wd;
+        if (EY(i)) qyy += wd;
+        if (EZ(i)) qzz += wd;
+        if (EX(i) && EY(i)) qxy += (EX(i) * EY(i) > 0) ? wd : -wd;
+        if (EX(i) && EZ(i)) qxz += (EX(i) * EZ(i) > 0) ? wd : -wd;
+        if (EY(i) && EZ(i)) qyz += (EY(i) * EZ(i) > 0) ? wd : -wd;
+    }
+    Forces F;
+    const float gp = -kp.G * pc;
+    const float ga = -kp.G_ads * pc * pc;
+    F.fx = gp * Sx + ga * Ax;
+    F.fy = gp * Sy + ga * Ay;
+    F.fz = gp * Sz + ga * Az;
+    const float kq = kp.kappa_G_half * pc;
+    F.qxx = kq * qxx;
+    F.qyy = kq * qyy;
+    F.qzz = kq * qzz;
+    F.qxy = kq * qxy;
+    F.qxz = kq * qxz;
+    F.qyz = kq * qyz;
+    F.s2 = Sx * Sx + Sy * Sy + Sz * Sz;
+    return F;
+}
+
+// ------------------------------------------------------------------ collision in moment space
+// m_bar* = m_bar - S (m_bar - m^eq) + (I - S/2) F~'   (Eq. e8), m^eq of Eq. e13,
+// F~ of Eq. e14 with the Eq. e17 modifications.  The conserved moments are
+// written in closed form: m*_0 = m_0, m*_{1..3} = m_{1..3} + F (exactly what
+// Eq. e8 gives once rho u = m_{1..3} + F/2).
+template <int Q>
+__device__ __forceinline__ void collide(const KParams& kp, float (&f)[Q], const Forces& Fo, float& rho_out,
+                                        float& ux_out, float& uy_out, float& uz_out) {
+    float m[Q];
+    to_moments<Q>(f, m);
+    const float rho = m[0];
+    const float inv_rho = 1.0f / rho;
+    const float Fx = Fo.fx + rho * kp.gx;
+    const float Fy = Fo.fy + rho * kp.gy;
+    const float Fz = Fo.fz + rho * kp.gz;
+    const float ux = (m[1] + 0.5f * Fx) * inv_rho;
+    const float uy = (m[2] + 0.5f * Fy) * inv_rho;
+    const float uz = (m[3] + 0.5f * Fz) * inv_rho;
+    rho_out = rho;
+    ux_out = ux;
+    uy_out = uy;
+    uz_out = uz;
+
+    float s_nu = kp.s[2], c_nu = kp.c[2], inv_tnu = kp.inv_tnu;
+    if (kp.variable_nu) {   // Sec. IV A: nu(rho), nu = (1/s_nu - 1/2) c_s^2
+        const float nu = kp.nu_v + kp.dnu_drho * (rho - kp.rho_v);
+        s_nu = 1.0f / (3.0f * nu + 0.5f);
+        c_nu = 1.0f - 0.5f * s_nu;
+        inv_tnu = 1.0f / (3.0f * nu);
+    }
+    const float cs2 = 1.0f / 3.0f, cs4 = 1.0f / 9.0f, cs6 = 1.0f / 27.0f;
+    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const float ru_x = rho * ux, ru_y = rho * uy, ru_z = rho * uz;
+    const float Fxux = Fx * ux, Fyuy = Fy * uy, Fzuz = Fz * uz;
+    const float Fu = Fxux + Fyuy + Fzuz;
+    const float Fxy = Fx * uy + Fy * ux, Fxz = Fx * uz + Fz * ux, Fyz = Fy * uz + Fz * uy;
+
+#define RELAX(k, meq, Ft, s, c) m[MP<Q>(k)] += (s) * ((meq) - m[MP<Q>(k)]) + (c) * (Ft)
+    m[1] += Fx;
+    m[2] += Fy;
+    m[3] += Fz;
+    RELAX(4, ru_x * uy, Fxy - Fo.qxy * inv_tnu, s_nu, c_nu);
+    RELAX(5, ru_x * uz, Fxz - Fo.qxz * inv_tnu, s_nu, c_nu);
+    RELAX(6, ru_y * uz, Fyz - Fo.qyz * inv_tnu, s_nu, c_nu);
+    RELAX(7, rho * (1.0f + uxx + uyy + uzz),
+          2.0f * Fu + kp.sigma_coef * Fo.s2 + kp.q7_coef * (Fo.qxx + Fo.qyy + Fo.qzz), kp.s[3], kp.c[3]);
+    RELAX(8, rho * (uxx - uyy), 2.0f * (Fxux - Fyuy) - (Fo.qxx - Fo.qyy) * inv_tnu, s_nu, c_nu);
+    RELAX(9, rho * (uxx - uzz), 2.0f * (Fxux - Fzuz) - (Fo.qxx - Fo.qzz) * inv_tnu, s_nu, c_nu);
+    RELAX(10, cs2 * ru_x, cs2 * Fx, kp.s[4], kp.c[4]);
+    RELAX(11, cs2 * ru_x, cs2 * Fx, kp.s[4], kp.c[4]);
+    RELAX(12, cs2 * ru_y, cs2 * Fy, kp.s[4], kp.c[4]);
+    RELAX(13, cs2 * ru_z, cs2 * Fz, kp.s[4], kp.c[4]);
+    RELAX(14, cs2 * ru_y, cs2 * Fy, kp.s[4], kp.c[4]);
+    RELAX(15, cs2 * ru_z, cs2 * Fz, kp.s[4], kp.c[4]);
+    if (Q == 27) RELAX(16, 0.0f, 0.0f, kp.s[5], kp.c[5]);
+    RELAX(17, cs2 * rho * (cs2 + uxx + uyy), 2.0f * cs2 * (Fxux + Fyuy), kp.s[6], kp.c[6]);
+    RELAX(18, cs2 * rho * (cs2 + uxx + uzz), 2.0f * cs2 * (Fxux + Fzuz), kp.s[6], kp.c[6]);
+    RELAX(19, cs2 * rho * (cs2 + uyy + uzz), 2.0f * cs2 * (Fyuy + Fzuz), kp.s[6], kp.c[6]);
+    if (Q == 27) {
+        RELAX(20, cs2 * ru_y * uz, cs2 * Fyz, kp.s[7], kp.c[7]);
+        RELAX(21, cs2 * ru_x * uz, cs2 * Fxz, kp.s[7], kp.c[7]);
+        RELAX(22, cs2 * ru_x * uy, cs2 * Fxy, kp.s[7], kp.c[7]);
+        RELAX(23, cs4 * ru_x, cs4 * Fx, kp.s[8], kp.c[8]);
+        RELAX(24, cs4 * ru_y, cs4 * Fy, kp.s[8], kp.c[8]);
+        RELAX(25, cs4 * ru_z, cs4 * Fz, kp.s[8], kp.c[8]);
+        RELAX(26, cs4 * rho * (uxx + uyy + uzz) + cs6 * rho, 2.0f * cs4 * Fu, kp.s[9], kp.c[9]);
+    }
+#undef RELAX
+    to_pops<Q>(m, f);
+}
+
+// ------------------------------------------------------------------ psi tile in shared memory
+// Block of BX x BY x BZ cells; the tile holds psi for the block plus a one-cell
+// halo (periodic wrap; 0 beyond a wall, where the solid bits take over).
+template <int BX, int BY, int BZ>
+struct PsiTile {
+    static constexpr int TX = BX + 2, TY = BY + 2, TZ = BZ + 2, SIZE = TX * TY * TZ;
+    float v[SIZE];
+
+    __device__ __forceinline__ void load(const KParams& kp, const float* __restrict__ psi, int x0, int y0, int z0,
+                                         int tid) {
+        const long long nxy = (long long)kp.nx * kp.ny;
+        for (int k = tid; k < SIZE; k += BX * BY * BZ) {
+            const int tx = k % TX, ty = (k / TX) % TY, tz = k / (TX * TY);
+            int gx = x0 - 1 + tx, gy = y0 - 1 + ty, gz = z0 - 1 + tz;
+            bool ok = true;
+            if (gx < 0) { ok &= !kp.wall_x; gx += kp.nx; } else if (gx >= kp.nx) { ok &= !kp.wall_x; gx -= kp.nx; }
+            if (gy < 0) { ok &= !kp.wall_y; gy += kp.ny; } else if (gy >= kp.ny) { ok &= !kp.wall_y; gy -= kp.ny; }
+            if (gz < 0) { ok &= !kp.wall_z; gz += kp.nz; } else if (gz >= kp.nz) { ok &= !kp.wall_z; gz -= kp.nz; }
+            // one wrap suffices for every cell an active thread reads; anything still outside is unused
+            ok = ok && gx >= 0 && gx < kp.nx && gy >= 0 && gy < kp.ny && gz >= 0 && gz < kp.nz;
+            v[k] = ok ? __ldg(psi + gz * nxy + (long long)gy * kp.nx + gx) : 0.0f;
+        }
+    }
+    __device__ __forceinline__ const float* at(int lx, int ly, int lz) const {
+        return v + (lz + 1) * TX * TY + (ly + 1) * TX + (lx + 1);
+    }
+};
+
+}  // namespace lbm

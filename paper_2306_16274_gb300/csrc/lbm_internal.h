@@ -1,0 +1,69 @@
+// Internal interface between the C ABI (capi.cu) and the per-lattice kernel
+// translation units (kernels_q19.cu, kernels_q27.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Status bits raised by kernels (read by lbm_sync).
+enum : unsigned { ST_UNSTABLE = 1u, ST_EOS_RANGE = 2u };
+
+// Everything a kernel needs, flattened to floats on the host (derived terms
+// precomputed in double, rounded once).
+struct KParams {
+    int nx, ny, nz;
+    int wall_x, wall_y, wall_z;   // 1 = half-way bounce-back walls on that axis
+    long long plane;              // stride between population planes (floats), >= ncell
+    long long ncell;              // nx * ny * nz
+    int multiphase;               // EOS present (psi, F_int, F_ads, Q, sigma term)
+    int eos;                      // 1 Carnahan-Starling, 2 piecewise linear
+    // Carnahan-Starling: p = rho RT g(eta) - a rho^2, eta = (b/4) rho
+    float cs_a, cs_b4, cs_RT;
+    double cs_a_d, cs_b4_d, cs_RT_d;
+    float psi_fp64_rho;           // rho >= this: evaluate the EOS and p - rho c_s^2 in FP64
+    // piecewise linear (Eq. e19)
+    float pw_rho1, pw_rho2, pw_tv, pw_tm, pw_tl, pw_p1, pw_p2;
+    float two_over_G;             // psi^2 = (2/G)(p_EOS - rho c_s^2)
+    double two_over_G_d;
+    float G;                      // Eq. e15
+    float G_ads;                  // Sec. III E
+    float kappa_G_half;           // kappa G / 2 of Eq. e18
+    float sigma_coef;             // 6 sigma G^2 / (1/s_e - 1/2): |F_int|^2 / psi^2 = G^2 |S|^2
+    float q7_coef;                // 4 / (5 (1/s_e - 1/2))
+    float s[10];                  // s0 s1 s2 s2b s3 s3b s4 s4b s5 s6
+    float c[10];                  // 1 - s/2
+    float inv_tnu;                // 1 / (1/s2 - 1/2)
+    int variable_nu;
+    float nu_v, dnu_drho, rho_v;  // nu(rho) = nu_v + dnu_drho (rho - rho_v)
+    float gx, gy, gz;             // body force per unit mass
+};
+
+// Launchers (one set per lattice).  parity: 0 = natural layout (even AA step),
+// 1 = swapped layout (odd AA step).  solids: walls or a solid mask exist.
+#define LBM_DECLARE_LAUNCHERS(Q)                                                                    \
+    cudaError_t launch_psi_q##Q(const KParams& kp, int parity, int solids, const float* f,          \
+                                float* psi, const uint32_t* nbmask, unsigned* status, cudaStream_t st); \
+    cudaError_t launch_collide_q##Q(const KParams& kp, int parity, int solids, float* f,             \
+                                    const float* psi, const uint32_t* nbmask, unsigned* status,      \
+                                    cudaStream_t st);                                               \
+    cudaError_t launch_init_q##Q(const KParams& kp, float* f, const float* rho, const float* u,     \
+                                 const uint32_t* nbmask, cudaStream_t st);                          \
+    cudaError_t launch_moments_q##Q(const KParams& kp, int parity, int solids, const float* f,      \
+                                    const float* psi, const uint32_t* nbmask, float* rho, float* u,  \
+                                    double* partials, int* nblocks, cudaStream_t st);               \
+    cudaError_t launch_gather_q##Q(const KParams& kp, int parity, int solids, const float* f,       \
+                                   const uint32_t* nbmask, float* out, cudaStream_t st);
+
+LBM_DECLARE_LAUNCHERS(19)
+LBM_DECLARE_LAUNCHERS(27)
+
+// Lattice-independent kernels (capi.cu)
+cudaError_t launch_nbmask(const KParams& kp, int Q, const uint8_t* solid, uint32_t* nbmask, cudaStream_t st);
+cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums, cudaStream_t st);
+
+// Number of blocks launch_moments_q* uses for partial sums (upper bound for the scratch size).
+long long moments_partial_blocks(const KParams& kp);
+
+}  // namespace lbm

@@ -1,0 +1,296 @@
+"""Python binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels behind the C ABI; this module
+converts Python / numpy / torch arguments into the plain pointers and sizes the
+ABI takes and turns status codes into exceptions.  PyTorch is used for device
+memory (output tensors) and streams.  There is no CPU fallback: if the library
+is missing or a call fails, an exception is raised.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+EOS = {"none": 0, "cs": 1, "piecewise": 2}
+BC = {"periodic": 0, "wall": 1}
+RATE_NAMES = ("s0", "s1", "s2", "s2b", "s3", "s3b", "s4", "s4b", "s5", "s6")
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_UNSTABLE",
+          5: "LBM_ERR_EOS_RANGE", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_STATE"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 3), ("eos", ctypes.c_int32), ("eos_p", ctypes.c_double * 5),
+        ("G", ctypes.c_double), ("G_ads", ctypes.c_double), ("kappa", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("s", ctypes.c_double * 10), ("variable_nu", ctypes.c_int32),
+        ("nu_l", ctypes.c_double), ("nu_v", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
+        ("g", ctypes.c_double * 3), ("psi_fp64_rho", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblbm.so (built in-tree by paper_2306_16274_gb300.build) and declare the ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2306_16274_gb300.build` "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, V, I32, I64, D = ctypes.c_void_p, None, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "lbm_default_params": (V, [ctypes.POINTER(lbm_params)]),
+        "lbm_create": (I32, [ctypes.POINTER(lbm_params), P, ctypes.POINTER(P)]),
+        "lbm_init_fields": (I32, [P, P, P, P, I32]),
+        "lbm_step": (I32, [P, I32]),
+        "lbm_sync": (I32, [P]),
+        "lbm_get_moments": (I32, [P, P, P, P, I32]),
+        "lbm_get_psi": (I32, [P, P, I32]),
+        "lbm_get_populations": (I32, [P, P, I32]),
+        "lbm_set_populations": (I32, [P, P, I32]),
+        "lbm_set_stream": (I32, [P, P]),
+        "lbm_set_kernel_timing": (I32, [P, I32]),
+        "lbm_get_kernel_timing": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "lbm_step_count": (I64, [P]),
+        "lbm_device_bytes": (ctypes.c_size_t, [P]),
+        "lbm_destroy": (V, [P]),
+        "lbm_last_error": (ctypes.c_char_p, [P]),
+        "lbm_status_string": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+@dataclass
+class Params:
+    """Mirror of lbm_params.  shape = (nx, ny, nz); bc per axis "periodic" / "wall";
+    eos "none" / "cs" (eos_p = a, b, R, T) / "piecewise" (rho1, rho2, theta_v, theta_m, theta_l);
+    rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library)."""
+    lattice: int = 19
+    shape: tuple = (32, 32, 32)
+    bc: tuple = ("periodic", "periodic", "periodic")
+    eos: str = "none"
+    eos_p: tuple = ()
+    G: float = -1.0
+    G_ads: float = 0.0
+    kappa: float = 0.0
+    sigma: float = 0.1
+    rates: dict = field(default_factory=dict)
+    variable_nu: bool = False
+    nu_l: float = 0.0
+    nu_v: float = 0.0
+    rho_l: float = 1.0
+    rho_v: float = 0.0
+    g: tuple = (0.0, 0.0, 0.0)
+    psi_fp64_rho: float = -1.0
+
+    def to_c(self):
+        c = lbm_params()
+        lib().lbm_default_params(ctypes.byref(c))
+        c.lattice = int(self.lattice)
+        c.nx, c.ny, c.nz = (int(v) for v in self.shape)
+        for a in range(3):
+            b = self.bc[a]
+            c.bc[a] = BC[b] if isinstance(b, str) else int(b)
+        c.eos = EOS[self.eos] if isinstance(self.eos, str) else int(self.eos)
+        for k, v in enumerate(self.eos_p):
+            c.eos_p[k] = float(v)
+        c.G, c.G_ads, c.kappa, c.sigma = float(self.G), float(self.G_ads), float(self.kappa), float(self.sigma)
+        for k, name in enumerate(RATE_NAMES):
+            if name in self.rates:
+                c.s[k] = float(self.rates[name])
+        c.variable_nu = 1 if self.variable_nu else 0
+        c.nu_l, c.nu_v, c.rho_l, c.rho_v = float(self.nu_l), float(self.nu_v), float(self.rho_l), float(self.rho_v)
+        for k in range(3):
+            c.g[k] = float(self.g[k])
+        c.psi_fp64_rho = float(self.psi_fp64_rho)
+        return c
+
+    @property
+    def ncell(self):
+        nx, ny, nz = self.shape
+        return int(nx) * int(ny) * int(nz)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a, n, dtype, name):
+    """(pointer, on_device, keepalive) for a torch tensor or array-like holding n elements."""
+    if a is None:
+        return None, None, None
+    mod = type(a).__module__
+    if mod.startswith("torch"):
+        torch = _torch()
+        t = a.detach().contiguous()
+        want = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        if t.dtype != want:
+            t = t.to(want)
+        if t.numel() != n:
+            raise ValueError(f"{name}: expected {n} elements, got {t.numel()}")
+        return t.data_ptr(), bool(t.is_cuda), t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.size != n:
+        raise ValueError(f"{name}: expected {n} elements, got {arr.size}")
+    return arr.ctypes.data, False, arr
+
+
+class Simulation:
+    """One lattice-Boltzmann domain on the current CUDA device (wraps an lbm_ctx)."""
+
+    def __init__(self, params: Params, stream=None):
+        self.params = params
+        self._L = lib()
+        self._c = params.to_c()
+        self.Q = int(params.lattice)
+        self.n = params.ncell
+        self.stream = _stream_handle(stream)
+        ctx = ctypes.c_void_p()
+        st = self._L.lbm_create(ctypes.byref(self._c), ctypes.c_void_p(self.stream), ctypes.byref(ctx))
+        if st != 0:
+            raise LBMError(st, self._L.lbm_last_error(None).decode())
+        self._ctx = ctx
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._L.lbm_last_error(self._ctx).decode())
+
+    def _same_side(self, flags):
+        flags = [f for f in flags if f is not None]
+        if flags and any(f != flags[0] for f in flags):
+            raise ValueError("all arrays of one call must be on the device or all on the host")
+        return int(flags[0]) if flags else 1
+
+    # ---------------------------------------------------------------- ABI calls
+    def init_fields(self, rho, u, solid=None):
+        pr, dr, kr = _ptr(rho, self.n, np.float32, "rho")
+        pu, du, ku = _ptr(u, 3 * self.n, np.float32, "u")
+        ps, ds, ks = _ptr(solid, self.n, np.uint8, "solid")
+        on_dev = self._same_side([dr, du, ds])
+        self._check(self._L.lbm_init_fields(self._ctx, pr, pu, ps, on_dev))
+        return self
+
+    def step(self, n=1):
+        self._check(self._L.lbm_step(self._ctx, int(n)))
+        return self
+
+    def sync(self):
+        self._check(self._L.lbm_sync(self._ctx))
+
+    def moments(self, device=True, sums=True):
+        """(rho, u, sums): rho (nz, ny, nx), u (3, nz, ny, nx) as torch CUDA tensors (device=True)
+        or numpy arrays; sums = FP64 (sum rho, sum rho u_x, sum rho u_y, sum rho u_z) over fluid cells."""
+        nx, ny, nz = self.params.shape
+        s = (ctypes.c_double * 4)()
+        if device:
+            torch = _torch()
+            rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+            u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+            self._check(self._L.lbm_get_moments(self._ctx, rho.data_ptr(), u.data_ptr(), s if sums else None, 1))
+        else:
+            rho = np.empty((nz, ny, nx), dtype=np.float32)
+            u = np.empty((3, nz, ny, nx), dtype=np.float32)
+            self._check(self._L.lbm_get_moments(self._ctx, rho.ctypes.data, u.ctypes.data, s if sums else None, 0))
+        return rho, u, (np.array(list(s)) if sums else None)
+
+    def moments_into(self, rho, u, sums=None):
+        """Fill caller-owned buffers (torch CUDA tensors or host arrays); sums: ctypes double[4] or None."""
+        pr, dr, kr = _ptr(rho, self.n, np.float32, "rho") if rho is not None else (None, None, None)
+        pu, du, ku = _ptr(u, 3 * self.n, np.float32, "u") if u is not None else (None, None, None)
+        on_dev = self._same_side([dr, du])
+        self._check(self._L.lbm_get_moments(self._ctx, pr, pu, sums, on_dev))
+
+    def psi(self, device=True):
+        nx, ny, nz = self.params.shape
+        if device:
+            torch = _torch()
+            out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+            self._check(self._L.lbm_get_psi(self._ctx, out.data_ptr(), 1))
+        else:
+            out = np.empty((nz, ny, nx), dtype=np.float32)
+            self._check(self._L.lbm_get_psi(self._ctx, out.ctypes.data, 0))
+        return out
+
+    def populations(self, device=True):
+        nx, ny, nz = self.params.shape
+        if device:
+            torch = _torch()
+            out = torch.empty((self.Q, nz, ny, nx), dtype=torch.float32, device="cuda")
+            self._check(self._L.lbm_get_populations(self._ctx, out.data_ptr(), 1))
+        else:
+            out = np.empty((self.Q, nz, ny, nx), dtype=np.float32)
+            self._check(self._L.lbm_get_populations(self._ctx, out.ctypes.data, 0))
+        return out
+
+    def set_populations(self, f):
+        p, d, k = _ptr(f, self.Q * self.n, np.float32, "f")
+        self._check(self._L.lbm_set_populations(self._ctx, p, int(d)))
+
+    def set_stream(self, stream):
+        self.stream = _stream_handle(stream)
+        self._check(self._L.lbm_set_stream(self._ctx, ctypes.c_void_p(self.stream)))
+
+    def set_kernel_timing(self, enable=True):
+        self._check(self._L.lbm_set_kernel_timing(self._ctx, 1 if enable else 0))
+
+    def kernel_timing(self):
+        """({'psi': ms, 'collide': ms}, {'psi': launches, 'collide': launches}) since timing was enabled."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int64 * 2)()
+        self._check(self._L.lbm_get_kernel_timing(self._ctx, ms, n))
+        return {"psi": ms[0], "collide": ms[1]}, {"psi": n[0], "collide": n[1]}
+
+    @property
+    def step_count(self):
+        return int(self._L.lbm_step_count(self._ctx))
+
+    @property
+    def device_bytes(self):
+        return int(self._L.lbm_device_bytes(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.lbm_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

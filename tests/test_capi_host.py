@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every
+function include/lbm.h declares, and rejects invalid parameters before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_16274_gb300 import build as B
+from paper_2306_16274_gb300 import lbm as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert "lbm_create" in names and "lbm_step" in names and "lbm_get_moments" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_params_struct_layout_matches_header(lib):
+    # the binding's ctypes mirror must have the C layout: defaults written by the library land
+    # in the right fields
+    p = L.lbm_params()
+    lib.lbm_default_params(ctypes.byref(p))
+    assert p.lattice == 19 and (p.nx, p.ny, p.nz) == (32, 32, 32)
+    assert list(p.s) == [1.0, 1.0, 1.2, 0.6, 1.2, 0.6, 1.2, 1.2, 1.2, 1.2]
+    assert p.G == -1.0 and p.sigma == 0.1 and p.psi_fp64_rho == -1.0
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(lattice=15), "lattice"),
+    (dict(shape=(0, 4, 4)), "nx"),
+    (dict(rates={"s2": 2.0}), "rates"),
+    (dict(rates={"s4": 0.0}), "rates"),
+    (dict(eos="cs", eos_p=(0.5, 4.0, 1.0, 0.03), G=0.0), "G"),
+    (dict(eos="piecewise", eos_p=(0.5, 0.1, 0.1, -0.01, 0.3)), "rho1"),
+    (dict(variable_nu=True, nu_l=0.01, nu_v=0.01, rho_l=1.0, rho_v=1.0), "variable"),
+    (dict(bc=(0, 2, 0)), "bc"),
+])
+def test_invalid_parameters_are_rejected(lib, change, msg):
+    kw = dict(lattice=19, shape=(4, 4, 4))
+    kw.update(change)
+    p = L.Params(**kw)
+    ctx = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(p.to_c()), None, ctypes.byref(ctx))
+    assert st == 1 and not ctx.value
+    assert msg in lib.lbm_last_error(None).decode()
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.lbm_step(None, 1) == 1
+    assert lib.lbm_sync(None) == 1
+    assert lib.lbm_step_count(None) == -1
+    lib.lbm_destroy(None)
+    assert lib.lbm_status_string(4) == b"LBM_ERR_UNSTABLE"

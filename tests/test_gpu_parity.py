@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same
+seeded inputs.  Tolerances: L-infinity error relative to the field's maximum,
+<= 1e-5 for single-phase and <= 1e-4 for multiphase runs after 100 steps (FP32
+kernels against an FP64 reference)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL_SINGLE = 1e-5
+TOL_MULTI = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+# ragged shapes: not multiples of the 32 x 4 x 2 block, several blocks per axis
+SHAPES = [(37, 13, 9), (20, 9, 7)]
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_single_phase_periodic(Q, shape):
+    d = dict(lattice=Q, shape=shape, rates={"s2": 1.3, "s3": 1.1, "s4": 1.4})
+    rho, u = W.perturbed(shape, seed=3)
+    sim = U.run_gpu(d, rho, u, steps=100)
+    ref = U.run_oracle(d, rho, u, steps=100)
+    er, eu, sg, so = U.compare_moments(sim, ref)
+    assert er < TOL_SINGLE and eu < TOL_SINGLE, (er, eu)
+    assert abs(sg[0] - so[0]) < 1e-6 * so[0]
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("steps", [1, 2, 3, 8])
+def test_populations_every_parity(Q, steps):
+    # element-wise populations after odd and even step counts (AA layout converted back)
+    shape = (35, 6, 5)
+    d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), g=(1e-5, 0.0, -2e-5))
+    rho, u = W.perturbed(shape, seed=5)
+    solid = W.random_mask(shape, 0.08, seed=9)
+    sim = U.run_gpu(d, rho, u, solid, steps=steps)
+    ref = U.run_oracle(d, rho, u, solid, steps=steps)
+    fg = sim.populations().cpu().numpy()
+    assert np.abs(fg - ref.f).max() < 1e-6 * np.abs(ref.f).max()
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_walls_solids_body_force(Q):
+    shape = (33, 10, 12)
+    d = dict(lattice=Q, shape=shape, bc=(0, 1, 1), g=(2e-5, 0.0, 0.0), rates={"s2": 0.9})
+    rho, u = W.perturbed(shape, seed=7, U=0.02)
+    solid = W.random_mask(shape, 0.05, seed=1)
+    sim = U.run_gpu(d, rho, u, solid, steps=100)
+    ref = U.run_oracle(d, rho, u, solid, steps=100)
+    er, eu, sg, so = U.compare_moments(sim, ref)
+    assert er < TOL_SINGLE and eu < TOL_SINGLE, (er, eu)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_psi_after_init(Q):
+    # psi of Sec. II C on both C-S branches (FP32 vapour side, FP64 liquid side) and for the
+    # piecewise EOS, element by element
+    shape = (34, 10, 6)
+    for eos, thr in ((U.cs_eos("T0.5"), -1.0), (U.cs_eos("T0.5"), 0.0), (U.pw_eos(), -1.0)):
+        kw, rl, rv = eos
+        d = dict(lattice=Q, shape=shape, psi_fp64_rho=thr, **kw)
+        rho, u = W.droplet(shape, 4.0, rl, rv)
+        sim = U.run_gpu(d, rho, u)
+        ref = U.run_oracle(d, rho, u)
+        psi_o = U.olbm.pseudopotential(U.olbm.density(ref.f, ref.solid), ref.solid, ref.p)
+        psi_g = sim.psi().cpu().numpy()
+        assert np.abs(psi_g - psi_o).max() < 2e-6 * psi_o.max()
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_static_droplet_laplace_config(Q):
+    # 32^3 periodic, C-S at 0.7 T_c, droplet R = 8 with the tanh profile (W = 2), kappa = 0
+    shape = (32, 32, 32)
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=Q, shape=shape, sigma=0.1, **kw)
+    rho, u = W.droplet(shape, 8.0, rl, rv)
+    sim = U.run_gpu(d, rho, u, steps=100)
+    ref = U.run_oracle(d, rho, u, steps=100)
+    er, eu, sg, so = U.compare_moments(sim, ref)
+    assert er < TOL_MULTI and eu < TOL_MULTI, (er, eu)
+    assert abs(sg[0] - so[0]) < 1e-6 * so[0]
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_many_droplets_large_density_ratio(Q):
+    # down-scaled at-scale workload: C-S at 0.5 T_c (ratio ~725), random spheres, kappa = 0.5
+    shape = (40, 36, 28)
+    kw, rl, rv = U.cs_eos("T0.5")
+    d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.5, **kw)
+    rho, u, _ = W.random_spheres(shape, rl, rv, 3.0, 7.0, seed=2306, target_fraction=0.10, gap=3.0)
+    sim = U.run_gpu(d, rho, u, steps=100)
+    ref = U.run_oracle(d, rho, u, steps=100)
+    er, eu, sg, so = U.compare_moments(sim, ref)
+    assert er < TOL_MULTI and eu < TOL_MULTI, (er, eu)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_impact_walls_wetting_variable_viscosity(Q):
+    # down-scaled impact: piecewise EOS, x/y periodic, walls in z with a wetting force,
+    # droplet moving toward the bottom wall, density-dependent viscosity, gravity
+    shape = (36, 34, 22)
+    kw, rl, rv = U.pw_eos()
+    d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), sigma=0.1, kappa=0.3, G_ads=-0.05,
+             variable_nu=True, nu_l=0.02, nu_v=0.1, rho_l=rl, rho_v=rv, g=(0.0, 0.0, -1e-6), **kw)
+    rho, u = W.impact(shape, 7.0, rl, rv, U=0.05, gap=3.0)
+    sim = U.run_gpu(d, rho, u, steps=100)
+    ref = U.run_oracle(d, rho, u, steps=100)
+    er, eu, sg, so = U.compare_moments(sim, ref)
+    assert er < TOL_MULTI and eu < TOL_MULTI, (er, eu)
+
+
+def test_host_pointers_match_device_pointers():
+    shape = (17, 9, 5)
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=19, shape=shape, sigma=0.1, **kw)
+    rho, u = W.droplet(shape, 3.0, rl, rv)
+    a = U.run_gpu(d, rho, u, steps=7, device=True)
+    b = U.run_gpu(d, rho, u, steps=7, device=False)
+    ra, ua, sa = a.moments(device=True)
+    rb, ub, sb = b.moments(device=False)
+    assert np.array_equal(ra.cpu().numpy(), rb) and np.array_equal(ua.cpu().numpy(), ub)
+    assert np.array_equal(sa, sb)
+
+
+def test_checkpoint_resume_is_bitwise():
+    shape = (33, 8, 6)
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=27, shape=shape, sigma=0.1, kappa=0.2, **kw)
+    rho, u = W.droplet(shape, 3.0, rl, rv)
+    a = U.run_gpu(d, rho, u, steps=11)
+    f = a.populations()
+    a.step(6)
+    b = U.run_gpu(d, rho, u)
+    b.set_populations(f)
+    b.step(6)
+    assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
+
+
+def test_deterministic_reruns():
+    shape = (40, 12, 10)
+    kw, rl, rv = U.cs_eos("T0.5")
+    d = dict(lattice=19, shape=shape, sigma=0.1, kappa=0.5, **kw)
+    rho, u, _ = W.random_spheres(shape, rl, rv, 2.0, 4.0, seed=1, gap=2.0)
+    a = U.run_gpu(d, rho, u, steps=20)
+    b = U.run_gpu(d, rho, u, steps=20)
+    ra, ua, sa = a.moments()
+    rb, ub, sb = b.moments()
+    assert np.array_equal(ra.cpu().numpy(), rb.cpu().numpy()) and np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_tiny_domains(Q):
+    # degenerate extents: a single cell periodic in every direction, and 1 x 1 x L columns
+    for shape in ((1, 1, 1), (1, 1, 16), (1, 5, 1)):
+        d = dict(lattice=Q, shape=shape, g=(1e-4, 0.0, 0.0))
+        rho, u = W.perturbed(shape, seed=2)
+        sim = U.run_gpu(d, rho, u, steps=10)
+        ref = U.run_oracle(d, rho, u, steps=10)
+        er, eu, _, _ = U.compare_moments(sim, ref)
+        assert er < TOL_SINGLE and eu < TOL_SINGLE, (shape, er, eu)
+
+
+def test_status_eos_range_and_unstable():
+    from paper_2306_16274_gb300 import LBMError
+    shape = (8, 8, 8)
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=19, shape=shape, sigma=0.1, **kw)
+    rho = np.full((8, 8, 8), 0.75)   # beyond the C-S range: psi^2 < 0
+    with pytest.raises(LBMError) as e:
+        U.run_gpu(d, rho, np.zeros((3, 8, 8, 8)), steps=1).sync()
+    assert e.value.status == 5
+    rho = np.full((8, 8, 8), 0.2)
+    rho[3, 3, 3] = np.nan
+    sim = U.run_gpu(dict(lattice=19, shape=shape), rho, np.zeros((3, 8, 8, 8)), steps=2)
+    with pytest.raises(LBMError) as e:
+        sim.sync()
+    assert e.value.status == 4
+    with pytest.raises(LBMError):     # sticky until re-initialised
+        sim.step(1)
+    sim.init_fields(np.full((8, 8, 8), 0.2, np.float32), np.zeros((3, 8, 8, 8), np.float32))
+    sim.step(1).sync()

@@ -103,14 +103,24 @@ def random_spheres(shape, rho_l, rho_v, r_min, r_max, seed=2306, target_fraction
         fails = 0
         spheres.append((c, r))
         vol += 4.0 / 3.0 * np.pi * r ** 3
-    x, y, z = _grid(shape)
     rho = np.full((nz, ny, nx), rho_v, dtype=np.float64)
     for (c, r) in spheres:
-        d = [x - c[0], y - c[1], z - c[2]]
+        # only the periodic bounding box of the sphere (plus the interface tail) is touched
+        h = int(np.ceil(r + 4.0 * W))
+        axes = []
         for k, n in enumerate((nx, ny, nz)):
-            d[k] = d[k] - n * np.round(d[k] / n)
-        dist = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
-        rho = np.maximum(rho, tanh_profile(dist, r, rho_l, rho_v, W))
+            lo = int(np.floor(c[k])) - h
+            idx = np.arange(lo, lo + 2 * h + 2)
+            d = idx - c[k]
+            if len(idx) >= n:      # box covers the whole axis: use the periodic minimum image
+                idx = np.arange(n)
+                d = idx - c[k]
+                d = d - n * np.round(d / n)
+            axes.append((idx % n, d))
+        (ix, dx), (iy, dy), (iz, dz) = axes
+        dist = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        sub = rho[np.ix_(iz, iy, ix)]
+        rho[np.ix_(iz, iy, ix)] = np.maximum(sub, tanh_profile(dist, r, rho_l, rho_v, W))
     return rho, np.zeros((3,) + rho.shape), [(tuple(float(v) for v in c), float(r)) for c, r in spheres]
 
 
