@@ -33,9 +33,10 @@ import workloads as W  # noqa: E402
 METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step)"
 UNIT = "MLUPS"
 SHAPE = (256, 256, 256)
-WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.5Tc, Maxwell coexistence densities, "
-            "random sphere droplets r~U[10,40] (seed 2306, liquid fraction>=0.10), kappa=0.5, sigma=0.1, "
-            "G=-1, default rates, FP32 populations (AA in place)")
+WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.5Tc, random sphere droplets r~U[10,40] "
+            "(seed 2306, liquid fraction>=0.10) started from the model's planar equilibrium (tanh, W and "
+            "coexistence densities of a relaxed slab), "
+            "kappa=0.5, sigma=0.1, G=-1, s2b=1.0 (other rates the paper's defaults), FP32 populations (AA in place)")
 
 
 def algorithmic_bytes(Q):
@@ -54,12 +55,21 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def workload_fields(shape, scale=1.0):
+def workload_fields(shape, scale=1.0, temperature="T0.5"):
+    """Random spheres.  At 0.5 T_c they start from the model's planar equilibrium (coexistence
+    densities and interface width of a relaxed slab, stored in workloads/constants.json); at 0.7 T_c
+    (profiling cases) from the Maxwell densities with W = 2."""
     c = W.constants()["cs"]
-    t = c["T0.5"]
-    rho, u, spheres = W.random_spheres(shape, t["rho_l"], t["rho_v"], 10.0 * scale, 40.0 * scale, seed=2306,
-                                       target_fraction=0.10, gap=4.0 * max(scale, 0.5))
-    params = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.5)
+    t = c[temperature]
+    if temperature == "T0.5":
+        eq = c["planar_T0.5"]
+        rl, rv, width = eq["rho_l"], eq["rho_v"], eq["W"]
+    else:
+        rl, rv, width = t["rho_l"], t["rho_v"], 2.0
+    rho, u, spheres = W.random_spheres(shape, rl, rv, 10.0 * scale, 40.0 * scale, seed=2306,
+                                       target_fraction=0.10, gap=4.0 * max(scale, 0.5), W=width)
+    params = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.5,
+                  rates={"s2b": 1.0})
     return rho, u, params
 
 
@@ -236,6 +246,7 @@ from oracle import lbm
 shape = {shape!r}
 rho, u, wp = bench.workload_fields(shape, scale={scale!r})
 rates = dict(lbm._mom.DEFAULT_RATES)
+rates.update(wp["rates"])
 p = lbm.Params(lattice={Q}, shape=shape, eos="cs", eos_p=tuple(wp["eos_p"]), G=-1.0, sigma=0.1, kappa=0.5,
                rates=rates)
 s = lbm.State.from_fields(p, rho, u)
@@ -317,6 +328,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-q27", action="store_true")
+    ap.add_argument("--temperature", default="0.5", choices=["0.5", "0.7"],
+                    help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
                     help="cubic edge; anything but 256 is a profiling case, not the benchmark workload")
     args = ap.parse_args()
@@ -334,7 +347,7 @@ def main():
     __graft_entry__.build()
     dist = init_dist(ws, local)
     torch.cuda.set_device(local)
-    rho, u, wparams = workload_fields(SHAPE, scale=SHAPE[0] / 256.0)
+    rho, u, wparams = workload_fields(SHAPE, scale=SHAPE[0] / 256.0, temperature="T" + args.temperature)
     n = float(np.prod(SHAPE))
     peak, peak_kind = measured_peaks()
 
@@ -359,7 +372,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if SHAPE == (256, 256, 256) else f"PROFILING CASE {SHAPE}",
+        "config": {"workload": WORKLOAD if (SHAPE == (256, 256, 256) and args.temperature == "0.5")
+                   else f"PROFILING CASE {SHAPE} T={args.temperature}Tc",
                    "lattice": 19, "shape": list(SHAPE), "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (populations %.2f GB per domain)" % (19 * 4 * n / 1e9)},
         "hbm_frac_step": step_gbs / peak,

@@ -11,7 +11,28 @@ import json
 import os
 import warnings
 
-from oracle import eos
+import numpy as np
+
+import workloads
+from oracle import eos, lbm
+
+
+def planar_equilibrium(cs, steps=10000):
+    """Relax a planar liquid slab (160 x 1 x 1, D3Q19, C-S at T = 0.5 T_c, G = -1, sigma = 0.1,
+    kappa = 0.5, s2b = 1.0) with the oracle and return its coexistence densities and the interface
+    width W = (rho_l - rho_v) / max |d rho / dx| of Eq. e23: the model's own equilibrium, used to
+    start droplets near equilibrium in the large-density-ratio workload."""
+    t = cs["T0.5"]
+    rates = dict(lbm._mom.DEFAULT_RATES)
+    rates["s2b"] = 1.0
+    p = lbm.Params(lattice=19, shape=(160, 1, 1), eos="cs", eos_p=(cs["a"], cs["b"], cs["R"], t["T"]), G=-1.0,
+                   sigma=0.1, kappa=0.5, rates=rates)
+    rho, u = workloads.slab((160, 1, 1), 80, t["rho_l"], t["rho_v"], W=5.0)
+    s = lbm.State.from_fields(p, rho, u).run(steps)
+    r = s.moments()[0][0, 0]
+    return {"rho_l": float(r.max()), "rho_v": float(r.min()),
+            "W": float((r.max() - r.min()) / np.abs(np.diff(r)).max()), "steps": steps,
+            "setup": "D3Q19 slab 160x1x1, sigma=0.1, kappa=0.5, s2b=1.0"}
 
 
 def main():
@@ -27,6 +48,7 @@ def main():
     r1, r2 = eos.piecewise_spinodals(0.001, 1.0, tv, tm, tl)
     out["piecewise"] = {"rho_v": 0.001, "rho_l": 1.0, "rho1": r1, "rho2": r2,
                         "theta_v": tv, "theta_m": tm, "theta_l": tl}
+    out["cs"]["planar_T0.5"] = planar_equilibrium(out["cs"])
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "constants.json")
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
