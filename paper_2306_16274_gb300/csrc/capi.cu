@@ -68,7 +68,7 @@ lbm_status validate(const lbm_params* p, std::string& why) {
     if (p->lattice != 19 && p->lattice != 27) { why = "lattice must be 19 or 27"; return LBM_ERR_ARG; }
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_ERR_ARG; }
     const long long n = (long long)p->nx * p->ny * p->nz;
-    if (n > (1LL << 40)) { why = "domain too large"; return LBM_ERR_ARG; }
+    if (n >= (1LL << 31)) { why = "domain too large: at most 2^31 - 1 cells"; return LBM_ERR_ARG; }
     for (int a = 0; a < 3; ++a)
         if (p->bc[a] != LBM_BC_PERIODIC && p->bc[a] != LBM_BC_WALL) { why = "bc must be 0 or 1"; return LBM_ERR_ARG; }
     for (int k = 0; k < 10; ++k)
@@ -266,6 +266,8 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
     cudaError_t e = cudaGetDevice(&c->device);
     const int stage_w = c->Q > 4 ? c->Q : 4;
     if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * sizeof(float));
+    if (e == cudaSuccess)
+        for (int i = 0; i < c->Q; ++i) c->kp.fq[i] = c->f + (size_t)i * plane;
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));

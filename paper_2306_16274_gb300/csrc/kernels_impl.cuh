@@ -39,48 +39,102 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
-constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;
+// Tiles of 32 x 8 cells in (x, y) march through a chunk of z planes.  psi planes
+// z-1, z, z+1 (with a one-cell x/y halo) sit in a four-slot shared-memory ring,
+// so each plane is read once per tile and one barrier per plane suffices.
+constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
+#ifndef LBM_ZM_BY
+#define LBM_ZM_BY 8
+#endif
+#ifndef LBM_ZM_MINB19
+#define LBM_ZM_MINB19 4
+#endif
+#ifndef LBM_ZM_MINB27
+#define LBM_ZM_MINB27 3
+#endif
+constexpr int ZM_BX = 32, ZM_BY = LBM_ZM_BY, ZM_MINB = LBM_Q == 19 ? LBM_ZM_MINB19 : LBM_ZM_MINB27;
+constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
+constexpr int ZM_NT = ZM_BX * ZM_BY;
+constexpr int ZM_SLOTS = (ZM_RP + ZM_NT - 1) / ZM_NT;  // psi loads per thread per plane
 
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) collide_kernel(KParams kp, float* __restrict__ f,
-                                                                       const float* __restrict__ psi,
-                                                                       const uint32_t* __restrict__ nbmask,
-                                                                       unsigned* status) {
-    __shared__ PsiTile<CS_BX, CS_BY, CS_BZ> tile;
-    const int x0 = blockIdx.x * CS_BX, y0 = blockIdx.y * CS_BY, z0 = blockIdx.z * CS_BZ;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    const int tid = threadIdx.x + CS_BX * (threadIdx.y + CS_BY * threadIdx.z);
-    const bool inside = x < kp.nx && y < kp.ny && z < kp.nz;
+__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
+                                                                const uint32_t* __restrict__ nbmask,
+                                                                unsigned* status, int zchunk) {
+    __shared__ float ring[4][ZM_RP];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
+    const int x0 = blockIdx.x * ZM_BX, y0 = blockIdx.y * ZM_BY, z0 = blockIdx.z * zchunk;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act_xy = x < kp.nx && y < kp.ny;
+    const uint32_t nxy = (uint32_t)kp.nx * (uint32_t)kp.ny;
 
-    Cell c;
-    uint32_t bits = 0u;
-    float p[Q];
-    bool active = false;
-    if (inside) {
-        c = make_cell(kp, x, y, z);
-        bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
-        active = !(bits & 1u);
-        if (active) gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    // this thread's share of each psi plane (x/y offsets fixed for the whole march)
+    uint32_t goff[ZM_SLOTS];
+    bool gok[ZM_SLOTS];
+#pragma unroll
+    for (int s = 0; s < ZM_SLOTS; ++s) {
+        const int k = tid + s * ZM_NT;
+        int gx = x0 - 1 + k % ZM_RX, gy = y0 - 1 + k / ZM_RX;
+        bool ok = k < ZM_RP;
+        if (gx < 0) { ok &= !kp.wall_x; gx += kp.nx; } else if (gx >= kp.nx) { ok &= !kp.wall_x; gx -= kp.nx; }
+        if (gy < 0) { ok &= !kp.wall_y; gy += kp.ny; } else if (gy >= kp.ny) { ok &= !kp.wall_y; gy -= kp.ny; }
+        ok = ok && gx >= 0 && gx < kp.nx && gy >= 0 && gy < kp.ny;
+        gok[s] = ok;
+        goff[s] = ok ? (uint32_t)gy * (uint32_t)kp.nx + (uint32_t)gx : 0u;
     }
-    if (MULTIPHASE) {
-        tile.load(kp, psi, x0, y0, z0, tid);
-        __syncthreads();
-    }
-    if (!active) return;
+    auto load_plane = [&](int zz, int slot) {
+        bool zok = true;
+        if (zz < 0) { zok = !kp.wall_z; zz += kp.nz; } else if (zz >= kp.nz) { zok = !kp.wall_z; zz -= kp.nz; }
+        const uint32_t zb = (uint32_t)zz * nxy;
+#pragma unroll
+        for (int s = 0; s < ZM_SLOTS; ++s) {
+            const int k = tid + s * ZM_NT;
+            if (k < ZM_RP) ring[slot][k] = (zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
+        }
+    };
 
-    Forces Fo;
+    Off32 o;
+    o.xo[0] = (uint32_t)wrap1(x - 1, kp.nx);
+    o.xo[1] = (uint32_t)x;
+    o.xo[2] = (uint32_t)wrap1(x + 1, kp.nx);
+    o.yo[0] = (uint32_t)wrap1(y - 1, kp.ny) * (uint32_t)kp.nx;
+    o.yo[1] = (uint32_t)y * (uint32_t)kp.nx;
+    o.yo[2] = (uint32_t)wrap1(y + 1, kp.ny) * (uint32_t)kp.nx;
+
     if (MULTIPHASE) {
-        Fo = stencil_forces<Q, SOLIDS>(kp, tile.at(threadIdx.x, threadIdx.y, threadIdx.z), PsiTile<CS_BX, CS_BY, CS_BZ>::TX,
-                                       PsiTile<CS_BX, CS_BY, CS_BZ>::TX * PsiTile<CS_BX, CS_BY, CS_BZ>::TY, bits);
-    } else {
-        Fo.fx = Fo.fy = Fo.fz = 0.f;
-        Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
-        Fo.s2 = 0.f;
+        load_plane(z0 - 1, 0);
+        load_plane(z0, 1);
     }
-    float rho, ux, uy, uz;
-    collide<Q>(kp, p, Fo, rho, ux, uy, uz);
-    if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
-    store<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+    const int zend = min(z0 + zchunk, kp.nz);
+    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
+    for (int z = z0, j = 0; z < zend; ++z, ++j) {
+        if (MULTIPHASE) {
+            load_plane(z + 1, (j + 2) & 3);
+            __syncthreads();
+        }
+        if (!act_xy) continue;
+        o.zo[0] = (uint32_t)wrap1(z - 1, kp.nz) * nxy;
+        o.zo[1] = (uint32_t)z * nxy;
+        o.zo[2] = (uint32_t)wrap1(z + 1, kp.nz) * nxy;
+        o.c = o.zo[1] + o.yo[1] + o.xo[1];
+        const uint32_t bits = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z) : 0u;
+        if (bits & 1u) continue;
+        float p[Q];
+        gather32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+        Forces Fo;
+        if (MULTIPHASE) {
+            Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
+                                            ZM_RX, bits);
+        } else {
+            Fo.fx = Fo.fy = Fo.fz = 0.f;
+            Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+            Fo.s2 = 0.f;
+        }
+        float rho, ux, uy, uz;
+        collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+        if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+        store32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+    }
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -259,19 +313,31 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
     return cudaGetLastError();
 }
 
+// z planes per block: enough blocks for a few waves of resident blocks on 152 SMs
+static int collide_zchunk(const KParams& kp) {
+    const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + ZM_BY - 1) / ZM_BY);
+    const long long target = 152LL * ZM_MINB * 4;
+    long long chunks = (target + cols - 1) / cols;
+    if (chunks > kp.nz) chunks = kp.nz;
+    if (chunks < 1) chunks = 1;
+    return (int)((kp.nz + chunks - 1) / chunks);
+}
+
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, float* f, const float* psi,
                                              const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
-    const dim3 g = cs_grid(kp), b(CS_BX, CS_BY, CS_BZ);
+    (void)f;   // addressed through kp.fq
+    const int zc = collide_zchunk(kp);
+    const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
     switch (key) {
-        case 0: collide_kernel<0, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 1: collide_kernel<0, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 2: collide_kernel<0, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 3: collide_kernel<0, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 4: collide_kernel<1, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 5: collide_kernel<1, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        case 6: collide_kernel<1, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
-        default: collide_kernel<1, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status); break;
+        case 0: collide_kernel<0, false, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 1: collide_kernel<0, false, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 2: collide_kernel<0, true, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 3: collide_kernel<0, true, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 4: collide_kernel<1, false, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 5: collide_kernel<1, false, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 6: collide_kernel<1, true, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        default: collide_kernel<1, true, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
     }
     return cudaGetLastError();
 }

@@ -300,6 +300,110 @@ __device__ __forceinline__ void collide(const KParams& kp, float (&f)[Q], const 
     to_pops<Q>(m, f);
 }
 
+// ------------------------------------------------------------------ 32-bit neighbourhood (z-marching kernels)
+// Offsets are cell indices (< 2^31); addresses are formed from the per-plane base
+// pointers kp.fq[i], which live in the kernel-parameter constant bank.
+struct Off32 {
+    uint32_t c;       // the cell
+    uint32_t xo[3];   // x-1, x, x+1 wrapped
+    uint32_t yo[3];   // rows y-1, y, y+1 wrapped, times nx
+    uint32_t zo[3];   // planes z-1, z, z+1 wrapped, times nx*ny
+    __device__ __forceinline__ uint32_t nb(int dx, int dy, int dz) const { return zo[dz + 1] + yo[dy + 1] + xo[dx + 1]; }
+};
+
+template <int Q>
+__device__ __forceinline__ uint32_t solid_bits32(const KParams& kp, const uint32_t* __restrict__ nbmask, uint32_t c,
+                                                 int x, int y, int z) {
+    uint32_t bits = nbmask ? __ldg(nbmask + c) : 0u;
+    const bool xl = kp.wall_x && x == 0, xh = kp.wall_x && x == kp.nx - 1;
+    const bool yl = kp.wall_y && y == 0, yh = kp.wall_y && y == kp.ny - 1;
+    const bool zl = kp.wall_z && z == 0, zh = kp.wall_z && z == kp.nz - 1;
+    if (xl | xh | yl | yh | zl | zh) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool s = (EX(i) < 0 && xl) || (EX(i) > 0 && xh) || (EY(i) < 0 && yl) || (EY(i) > 0 && yh) ||
+                           (EZ(i) < 0 && zl) || (EZ(i) > 0 && zh);
+            bits |= s ? (1u << i) : 0u;
+        }
+    }
+    return bits;
+}
+
+template <int Q, int PARITY, bool SOLIDS>
+__device__ __forceinline__ void gather32(const KParams& kp, const Off32& o, uint32_t bits, float (&p)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0) {
+            p[i] = __ldg(kp.fq[i] + o.c);
+        } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
+            p[i] = __ldg(kp.fq[i] + o.c);
+        } else {
+            p[i] = __ldg(kp.fq[OPP(i)] + o.nb(-EX(i), -EY(i), -EZ(i)));
+        }
+    }
+}
+
+template <int Q, int PARITY, bool SOLIDS>
+__device__ __forceinline__ void store32(const KParams& kp, const Off32& o, uint32_t bits, const float (&p)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0) {
+            kp.fq[OPP(i)][o.c] = p[i];
+        } else if (SOLIDS && ((bits >> i) & 1u)) {
+            kp.fq[OPP(i)][o.c] = p[i];
+        } else {
+            kp.fq[i][o.nb(EX(i), EY(i), EZ(i))] = p[i];
+        }
+    }
+}
+
+// Forces from three psi planes (z-1, z, z+1); each pointer addresses psi(x) within its plane,
+// x stride 1 and y stride sy.
+template <int Q, bool SOLIDS>
+__device__ __forceinline__ Forces stencil_forces3(const KParams& kp, const float* pm, const float* p0, const float* pp,
+                                                  int sy, uint32_t bits) {
+    const float pc = p0[0];
+    float Sx = 0.f, Sy = 0.f, Sz = 0.f, Ax = 0.f, Ay = 0.f, Az = 0.f;
+    float qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float* pl = EZ(i) < 0 ? pm : (EZ(i) > 0 ? pp : p0);
+        float pn = pl[EX(i) + EY(i) * sy];
+        if (SOLIDS && ((bits >> i) & 1u)) {
+            pn = pc;
+            Ax += WN<Q>(i) * EX(i);
+            Ay += WN<Q>(i) * EY(i);
+            Az += WN<Q>(i) * EZ(i);
+        }
+        const float wp = WN<Q>(i) * pn;
+        if (EX(i)) Sx += EX(i) > 0 ? wp : -wp;
+        if (EY(i)) Sy += EY(i) > 0 ? wp : -wp;
+        if (EZ(i)) Sz += EZ(i) > 0 ? wp : -wp;
+        const float wd = WN<Q>(i) * (pn - pc);
+        if (EX(i)) qxx += wd;
+        if (EY(i)) qyy += wd;
+        if (EZ(i)) qzz += wd;
+        if (EX(i) && EY(i)) qxy += (EX(i) * EY(i) > 0) ? wd : -wd;
+        if (EX(i) && EZ(i)) qxz += (EX(i) * EZ(i) > 0) ? wd : -wd;
+        if (EY(i) && EZ(i)) qyz += (EY(i) * EZ(i) > 0) ? wd : -wd;
+    }
+    Forces F;
+    const float gp = -kp.G * pc;
+    const float ga = -kp.G_ads * pc * pc;
+    F.fx = gp * Sx + ga * Ax;
+    F.fy = gp * Sy + ga * Ay;
+    F.fz = gp * Sz + ga * Az;
+    const float kq = kp.kappa_G_half * pc;
+    F.qxx = kq * qxx;
+    F.qyy = kq * qyy;
+    F.qzz = kq * qzz;
+    F.qxy = kq * qxy;
+    F.qxz = kq * qxz;
+    F.qyz = kq * qyz;
+    F.s2 = Sx * Sx + Sy * Sy + Sz * Sz;
+    return F;
+}
+
 // ------------------------------------------------------------------ psi tile in shared memory
 // Block of BX x BY x BZ cells; the tile holds psi for the block plus a one-cell
 // halo (periodic wrap; 0 beyond a wall, where the solid bits take over).

@@ -13,7 +13,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbm.so")
+# LBM_LIBRARY may point at another build of the same ABI (e.g. a tuning variant)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "liblbm.so")
 
 EOS = {"none": 0, "cs": 1, "piecewise": 2}
 BC = {"periodic": 0, "wall": 1}

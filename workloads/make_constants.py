@@ -40,7 +40,7 @@ def main():
     a, b, R = 0.5, 4.0, 1.0
     rho_c, T_c = eos.cs_critical_point(a, b, R)
     out = {"cs": {"a": a, "b": b, "R": R, "rho_c": rho_c, "T_c": T_c}}
-    for frac in (0.7, 0.5):
+    for frac in (0.7, 0.6, 0.55, 0.5):
         T = frac * T_c
         rv, rl = eos.cs_maxwell(a, b, R, T)
         out["cs"][f"T{frac}"] = {"T": T, "rho_v": rv, "rho_l": rl}
