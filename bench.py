@@ -1,10 +1,11 @@
 """Benchmark of the fused non-orthogonal MRT pseudopotential step on GB300.
 
 Workload (the paper's method at scale, one domain per GPU): 256^3 periodic,
-Carnahan-Starling EOS (a = 0.5, b = 4, R = 1) at T = 0.5 T_c with the Maxwell
+Carnahan-Starling EOS (a = 0.5, b = 4, R = 1) at T = 0.6 T_c with the Maxwell
 coexistence densities, random sphere droplets (radii uniform in [10, 40],
 numpy seed 2306, liquid fraction >= 0.10) in vapour, surface-tension tuning
-kappa = 0.5, sigma = 0.1, FP32 populations.  The headline value is D3Q19
+kappa = 0.5, sigma = 0.1, the paper's default relaxation rates, FP32
+populations.  The headline value is D3Q19
 MLUPS; the D3Q27 lattice is measured in the same run and reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -33,10 +34,10 @@ import workloads as W  # noqa: E402
 METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step)"
 UNIT = "MLUPS"
 SHAPE = (256, 256, 256)
-WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.5Tc, random sphere droplets r~U[10,40] "
-            "(seed 2306, liquid fraction>=0.10) started from the model's planar equilibrium (tanh, W and "
-            "coexistence densities of a relaxed slab), "
-            "kappa=0.5, sigma=0.1, G=-1, s2b=1.0 (other rates the paper's defaults), FP32 populations (AA in place)")
+WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves the EOS range within 100 steps "
+            "at this droplet size, in the FP64 oracle as on the GPU), Maxwell coexistence densities (ratio 132), "
+            "random sphere droplets r~U[10,40] (seed 2306, liquid fraction>=0.10, tanh W=3), kappa=0.5, "
+            "sigma=0.1, G=-1, the paper's default rates, FP32 populations (AA in place)")
 
 
 def algorithmic_bytes(Q):
@@ -55,21 +56,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def workload_fields(shape, scale=1.0, temperature="T0.5"):
-    """Random spheres.  At 0.5 T_c they start from the model's planar equilibrium (coexistence
-    densities and interface width of a relaxed slab, stored in workloads/constants.json); at 0.7 T_c
-    (profiling cases) from the Maxwell densities with W = 2."""
+def workload_fields(shape, scale=1.0, temperature="T0.6", r_min=10.0):
+    """Random sphere droplets in vapour between the Maxwell coexistence densities of the C-S EOS at
+    the given temperature, tanh interfaces (W = 3 at 0.6 T_c, 2 at 0.7 T_c), kappa = 0.5,
+    sigma = 0.1, G = -1 and the paper's default relaxation rates."""
     c = W.constants()["cs"]
     t = c[temperature]
-    if temperature == "T0.5":
-        eq = c["planar_T0.5"]
-        rl, rv, width = eq["rho_l"], eq["rho_v"], eq["W"]
-    else:
-        rl, rv, width = t["rho_l"], t["rho_v"], 2.0
-    rho, u, spheres = W.random_spheres(shape, rl, rv, 10.0 * scale, 40.0 * scale, seed=2306,
-                                       target_fraction=0.10, gap=4.0 * max(scale, 0.5), W=width)
-    params = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.5,
-                  rates={"s2b": 1.0})
+    width = 3.0 if temperature == "T0.6" else 2.0
+    rho, u, spheres = W.random_spheres(shape, t["rho_l"], t["rho_v"], r_min * scale,
+                                       40.0 * scale, seed=2306, target_fraction=0.10, gap=4.0, W=width)
+    params = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.5)
     return rho, u, params
 
 
@@ -244,9 +240,8 @@ sys.path.insert(0, {root!r})
 import bench, workloads as W
 from oracle import lbm
 shape = {shape!r}
-rho, u, wp = bench.workload_fields(shape, scale={scale!r})
+rho, u, wp = bench.workload_fields(shape, scale={scale!r}, r_min=5.0 / {scale!r})
 rates = dict(lbm._mom.DEFAULT_RATES)
-rates.update(wp["rates"])
 p = lbm.Params(lattice={Q}, shape=shape, eos="cs", eos_p=tuple(wp["eos_p"]), G=-1.0, sigma=0.1, kappa=0.5,
                rates=rates)
 s = lbm.State.from_fields(p, rho, u)
@@ -288,7 +283,7 @@ def reference_arm(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / r["steps"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " -- oracle sample: 64^3 copy (radii scaled 1/4), one step per step",
+            "config": {"workload": WORKLOAD + " -- oracle sample: 64^3 copy (radii U[5,10]), one step per step",
                        "lattice": Q, "shape": list(shape)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{shape[0]}^3 copy of the workload, {r['steps']} oracle steps"},
@@ -328,7 +323,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-q27", action="store_true")
-    ap.add_argument("--temperature", default="0.5", choices=["0.5", "0.7"],
+    ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
                     help="cubic edge; anything but 256 is a profiling case, not the benchmark workload")
@@ -372,7 +367,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if (SHAPE == (256, 256, 256) and args.temperature == "0.5")
+        "config": {"workload": WORKLOAD if (SHAPE == (256, 256, 256) and args.temperature == "0.6")
                    else f"PROFILING CASE {SHAPE} T={args.temperature}Tc",
                    "lattice": 19, "shape": list(SHAPE), "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (populations %.2f GB per domain)" % (19 * 4 * n / 1e9)},
@@ -401,7 +396,7 @@ def main():
         try:
             cb = oracle_timing(19, args.cpu_seconds)
             line["cpu_baseline"] = {"value": cb["mlups"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"64^3 copy of the workload (radii scaled 1/4), {cb['steps']} FP64 "
+                                    "sample": f"64^3 copy of the workload (radii U[5,10]), {cb['steps']} FP64 "
                                               f"oracle steps in {cb['seconds']:.1f} s, one thread"}
         except Exception as exc:  # the baseline is context; never lose the GPU line over it
             line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}

@@ -39,18 +39,20 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
-// Tiles of 32 x 8 cells in (x, y) march through a chunk of z planes.  psi planes
+// Tiles of 32 x ZM_BY cells in (x, y) march through a chunk of z planes.  psi planes
 // z-1, z, z+1 (with a one-cell x/y halo) sit in a four-slot shared-memory ring,
 // so each plane is read once per tile and one barrier per plane suffices.
 constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
+// tile height and blocks per SM (register cap 64 for D3Q19, 85 for D3Q27): best of a
+// measured sweep of (8, 4, 3), (8, 3, 2), (4, 8, 6), (8, 5, 4) on 256^3
 #ifndef LBM_ZM_BY
-#define LBM_ZM_BY 8
+#define LBM_ZM_BY 4
 #endif
 #ifndef LBM_ZM_MINB19
-#define LBM_ZM_MINB19 4
+#define LBM_ZM_MINB19 8
 #endif
 #ifndef LBM_ZM_MINB27
-#define LBM_ZM_MINB27 3
+#define LBM_ZM_MINB27 6
 #endif
 constexpr int ZM_BX = 32, ZM_BY = LBM_ZM_BY, ZM_MINB = LBM_Q == 19 ? LBM_ZM_MINB19 : LBM_ZM_MINB27;
 constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
