@@ -153,13 +153,19 @@ def barrier(dist):
         dist.barrier()
 
 
-def max_over_ranks(dist, value):
+def max_over_ranks(dist, value, device="cuda"):
+    """Largest value over all ranks (the slowest replica sets the job time)."""
     if dist is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mlups(world_size, cells, steps, ms_max):
+    """Whole-job throughput of N replicas: all ranks' cell updates over the slowest rank's time."""
+    return world_size * cells * steps / (ms_max * 1e-3) / 1e6
 
 
 # ---------------------------------------------------------------- our arm
@@ -352,7 +358,7 @@ def main():
     r19 = run_lattice(19, rho, u, wparams, args.steps, args.warmup, dist, clocks)
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(dist, r19["ms"])
-    value = ws * n * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(ws, n, args.steps, ms)
     r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
     e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
     if rank != 0:
