@@ -169,8 +169,31 @@ size_t lbm_device_bytes(const lbm_ctx* ctx);
 /* Frees the device state.  Waits for the stream first.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 
-/* Message of the last error on ctx (ctx == NULL: the last failed lbm_create
- * on this thread).  Never NULL. */
+/* Totals without allocation.  The paper has no counterpart: this is a service
+ * for callers that must not allocate device memory while they run (code being
+ * recorded into a CUDA graph, hosts whose device memory is pre-budgeted by their
+ * own allocator, real-time loops that cannot block on cudaMalloc/cudaFree).
+ * Computes, in FP64 and in a fixed order (deterministic), totals[0] = sum rho,
+ * totals[1..3] = sum rho u_x, sum rho u_y, sum rho u_z over ncell cells of
+ * caller-held DEVICE arrays rho (ncell floats) and u (3 ncell floats, the
+ * layout lbm_get_moments writes); totals is a DEVICE pointer to 4 doubles.
+ * Enqueued on cuda_stream (NULL = legacy default stream); does not wait.
+ * It calls no cudaMalloc / cudaFree: its scratch (one partial sum per block)
+ * is a fixed 512 KB device array in the library that every GPU loading the
+ * library holds until the process exits, so ncell is limited to
+ * LBM_NOALLOC_MAX_CELLS; larger ncell (or ncell < 1, or a NULL pointer) returns
+ * LBM_ERR_ARG with a message in lbm_last_error(NULL).  The first call on a
+ * device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  All calls on one
+ * device share the array: calls that may overlap on that GPU (e.g. on two
+ * streams) race; serialise them.  The partials are rewritten by every call, so
+ * no state carries over between calls. */
+#define LBM_NOALLOC_MAX_CELLS 33554432
+lbm_status lbm_field_totals_noalloc(const float* rho, const float* u, int64_t ncell, double* totals,
+                                    void* cuda_stream);
+
+/* Message of the last error on ctx (ctx == NULL: the last failed lbm_create or
+ * lbm_field_totals_noalloc on this thread).  Never NULL. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* Name of a status code. */

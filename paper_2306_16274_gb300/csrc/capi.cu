@@ -536,6 +536,8 @@ cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums
     return cudaGetLastError();
 }
 
+void set_thread_error(const char* msg) { g_create_error = msg; }
+
 long long moments_partial_blocks(const KParams& kp) {
     // matches the collide/moments launch shape (32 x 4 x 2 cells per block)
     return (long long)((kp.nx + 31) / 32) * ((kp.ny + 3) / 4) * ((kp.nz + 1) / 2);

@@ -64,6 +64,9 @@ LBM_DECLARE_LAUNCHERS(27)
 cudaError_t launch_nbmask(const KParams& kp, int Q, const uint8_t* solid, uint32_t* nbmask, cudaStream_t st);
 cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums, cudaStream_t st);
 
+// Sets the message lbm_last_error(NULL) returns on this thread (context-free entry points).
+void set_thread_error(const char* msg);
+
 // Number of blocks launch_moments_q* uses for partial sums (upper bound for the scratch size).
 long long moments_partial_blocks(const KParams& kp);
 

@@ -71,6 +71,7 @@ def lib():
         "lbm_destroy": (V, [P]),
         "lbm_last_error": (ctypes.c_char_p, [P]),
         "lbm_status_string": (ctypes.c_char_p, [I32]),
+        "lbm_field_totals_noalloc": (I32, [P, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -129,6 +130,23 @@ class Params:
     def ncell(self):
         nx, ny, nz = self.shape
         return int(nx) * int(ny) * int(nz)
+
+
+def field_totals_noalloc(rho, u, totals, stream=None):
+    """lbm_field_totals_noalloc: FP64 (sum rho, sum rho u_x, sum rho u_y, sum rho u_z) of caller-held
+    CUDA tensors rho (n floats) and u (3 n floats) into the caller's CUDA tensor `totals` (4 doubles),
+    enqueued on `stream`.  For callers that must not allocate device memory while they run (graph
+    capture, pre-budgeted allocators, real-time loops): the library uses a fixed scratch array instead
+    of cudaMalloc, so n is limited to LBM_NOALLOC_MAX_CELLS = 33554432 and calls that overlap on one
+    GPU race.  Make the first call on a device before any stream capture."""
+    L = lib()
+    n = int(rho.numel())
+    if int(u.numel()) != 3 * n or int(totals.numel()) != 4:
+        raise ValueError("u must hold 3 n floats and totals 4 doubles")
+    st = L.lbm_field_totals_noalloc(rho.data_ptr(), u.data_ptr(), n, totals.data_ptr(),
+                                    ctypes.c_void_p(_stream_handle(stream)))
+    if st != 0:
+        raise LBMError(st, L.lbm_last_error(None).decode())
 
 
 def _torch():
