@@ -40,8 +40,10 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
 // Tiles of 32 x ZM_BY cells in (x, y) march through a chunk of z planes.  psi planes
-// z-1, z, z+1 (with a one-cell x/y halo) sit in a four-slot shared-memory ring,
-// so each plane is read once per tile and one barrier per plane suffices.
+// z-1, z, z+1 (with a one-cell x/y halo) sit in a four-slot shared-memory ring, so
+// each plane is read once per tile.  The populations of plane z+1 (AA gather) and
+// psi plane z+2 are fetched with cp.async into shared memory while plane z is being
+// computed; one barrier per plane orders the copies and the ring reuse.
 constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
 // tile height and blocks per SM (register cap 64 for D3Q19, 85 for D3Q27): best of a
 // measured sweep of (8, 4, 3), (8, 3, 2), (4, 8, 6), (8, 5, 4) on 256^3
@@ -63,12 +65,16 @@ template <int PARITY, bool SOLIDS, bool MULTIPHASE>
 __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
                                                                 const uint32_t* __restrict__ nbmask,
                                                                 unsigned* status, int zchunk) {
+    // ring: psi planes (4 slots); pops: two stages of this block's populations, [stage][i][thread]
     __shared__ float ring[4][ZM_RP];
+    __shared__ float pops[2][Q][ZM_NT];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x0 = blockIdx.x * ZM_BX, y0 = blockIdx.y * ZM_BY, z0 = blockIdx.z * zchunk;
     const int x = x0 + tx, y = y0 + ty;
     const bool act_xy = x < kp.nx && y < kp.ny;
     const uint32_t nxy = (uint32_t)kp.nx * (uint32_t)kp.ny;
+    const int zend = min(z0 + zchunk, kp.nz);
+    const int nplanes = zend - z0;
 
     // this thread's share of each psi plane (x/y offsets fixed for the whole march)
     uint32_t goff[ZM_SLOTS];
@@ -84,6 +90,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
         gok[s] = ok;
         goff[s] = ok ? (uint32_t)gy * (uint32_t)kp.nx + (uint32_t)gx : 0u;
     }
+    // psi plane zz (wrapped, or zeros beyond a wall) into ring slot `slot`
     auto load_plane = [&](int zz, int slot) {
         bool zok = true;
         if (zz < 0) { zok = !kp.wall_z; zz += kp.nz; } else if (zz >= kp.nz) { zok = !kp.wall_z; zz -= kp.nz; }
@@ -91,7 +98,10 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
 #pragma unroll
         for (int s = 0; s < ZM_SLOTS; ++s) {
             const int k = tid + s * ZM_NT;
-            if (k < ZM_RP) ring[slot][k] = (zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
+            if (k < ZM_RP) {
+                if (zok && gok[s]) cp_async4(&ring[slot][k], psi + zb + goff[s]);
+                else ring[slot][k] = 0.0f;
+            }
         }
     };
 
@@ -102,41 +112,70 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     o.yo[0] = (uint32_t)wrap1(y - 1, kp.ny) * (uint32_t)kp.nx;
     o.yo[1] = (uint32_t)y * (uint32_t)kp.nx;
     o.yo[2] = (uint32_t)wrap1(y + 1, kp.ny) * (uint32_t)kp.nx;
-
-    if (MULTIPHASE) {
-        load_plane(z0 - 1, 0);
-        load_plane(z0, 1);
-    }
-    const int zend = min(z0 + zchunk, kp.nz);
-    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
-    for (int z = z0, j = 0; z < zend; ++z, ++j) {
-        if (MULTIPHASE) {
-            load_plane(z + 1, (j + 2) & 3);
-            __syncthreads();
-        }
-        if (!act_xy) continue;
+    auto set_plane = [&](int z) {
         o.zo[0] = (uint32_t)wrap1(z - 1, kp.nz) * nxy;
         o.zo[1] = (uint32_t)z * nxy;
         o.zo[2] = (uint32_t)wrap1(z + 1, kp.nz) * nxy;
         o.c = o.zo[1] + o.yo[1] + o.xo[1];
-        const uint32_t bits = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z) : 0u;
-        if (bits & 1u) continue;
-        float p[Q];
-        gather32<Q, PARITY, SOLIDS>(kp, o, bits, p);
-        Forces Fo;
-        if (MULTIPHASE) {
-            Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
-                                            ZM_RX, bits);
-        } else {
-            Fo.fx = Fo.fy = Fo.fz = 0.f;
-            Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
-            Fo.s2 = 0.f;
-        }
-        float rho, ux, uy, uz;
-        collide<Q>(kp, p, Fo, rho, ux, uy, uz);
-        if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
-        store32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+    };
+    // solid bits of plane z (interior solids from nbmask, walls from the position)
+    auto plane_bits = [&](int z) -> uint32_t {
+        return SOLIDS ? solid_bits32<Q>(kp, nbmask, o.zo[1] + o.yo[1] + o.xo[1], x, y, z) : 0u;
+    };
+
+    // prologue: psi planes z0-1, z0, z0+1 and the populations of plane z0
+    uint32_t bits_cur = 0u;
+    if (MULTIPHASE) {
+        load_plane(z0 - 1, 0);
+        load_plane(z0, 1);
+        load_plane(z0 + 1, 2);
     }
+    if (act_xy) {
+        set_plane(z0);
+        bits_cur = plane_bits(z0);
+        if (!(bits_cur & 1u)) gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_cur, &pops[0][0][tid], ZM_NT);
+    }
+    cp_async_commit();
+
+    for (int j = 0; j < nplanes; ++j) {
+        const int z = z0 + j;
+        cp_async_wait_all();   // this thread's copies for plane z (and psi plane z+1)
+        __syncthreads();       // everyone's copies visible; everyone finished plane z-1
+        // prefetch plane z+1 (populations) and psi plane z+2 while plane z is computed
+        uint32_t bits_next = 0u;
+        if (j + 1 < nplanes) {
+            if (MULTIPHASE) load_plane(z + 2, (j + 3) & 3);
+            if (act_xy) {
+                set_plane(z + 1);
+                bits_next = plane_bits(z + 1);
+                if (!(bits_next & 1u))
+                    gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_next, &pops[(j + 1) & 1][0][tid], ZM_NT);
+            }
+        }
+        cp_async_commit();
+        if (act_xy && !(bits_cur & 1u)) {
+            set_plane(z);
+            float p[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) p[i] = pops[j & 1][i][tid];
+            Forces Fo;
+            if (MULTIPHASE) {
+                const int lc = (ty + 1) * ZM_RX + tx + 1;
+                Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
+                                                ZM_RX, bits_cur);
+            } else {
+                Fo.fx = Fo.fy = Fo.fz = 0.f;
+                Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+                Fo.s2 = 0.f;
+            }
+            float rho, ux, uy, uz;
+            collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+            if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+            store32<Q, PARITY, SOLIDS>(kp, o, bits_cur, p);
+        }
+        bits_cur = bits_next;
+    }
+    cp_async_wait_all();
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -325,6 +364,23 @@ static int collide_zchunk(const KParams& kp) {
     return (int)((kp.nz + chunks - 1) / chunks);
 }
 
+// Launches one collide_kernel instantiation; the first launch asks for the largest shared-memory
+// carveout so that ZM_MINB blocks (with their population stages) fit on an SM.
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const float* psi,
+                                   const uint32_t* nbmask, unsigned* status, int zc) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    collide_kernel<PARITY, SOLIDS, MULTIPHASE><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc);
+    return cudaGetLastError();
+}
+
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, float* f, const float* psi,
                                              const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
     (void)f;   // addressed through kp.fq
@@ -332,16 +388,15 @@ cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int 
     const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
     switch (key) {
-        case 0: collide_kernel<0, false, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 1: collide_kernel<0, false, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 2: collide_kernel<0, true, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 3: collide_kernel<0, true, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 4: collide_kernel<1, false, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 5: collide_kernel<1, false, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        case 6: collide_kernel<1, true, false><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
-        default: collide_kernel<1, true, true><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc); break;
+        case 0: return launch_collide_variant<0, false, false>(g, b, st, kp, psi, nbmask, status, zc);
+        case 1: return launch_collide_variant<0, false, true>(g, b, st, kp, psi, nbmask, status, zc);
+        case 2: return launch_collide_variant<0, true, false>(g, b, st, kp, psi, nbmask, status, zc);
+        case 3: return launch_collide_variant<0, true, true>(g, b, st, kp, psi, nbmask, status, zc);
+        case 4: return launch_collide_variant<1, false, false>(g, b, st, kp, psi, nbmask, status, zc);
+        case 5: return launch_collide_variant<1, false, true>(g, b, st, kp, psi, nbmask, status, zc);
+        case 6: return launch_collide_variant<1, true, false>(g, b, st, kp, psi, nbmask, status, zc);
+        default: return launch_collide_variant<1, true, true>(g, b, st, kp, psi, nbmask, status, zc);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, float* f, const float* rho, const float* u,

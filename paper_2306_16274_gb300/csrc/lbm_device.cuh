@@ -357,6 +357,31 @@ __device__ __forceinline__ void store32(const KParams& kp, const Off32& o, uint3
     }
 }
 
+// ------------------------------------------------------------------ asynchronous global -> shared copies
+// cp.async (4-byte form, any 4-byte-aligned address): the copy is in flight without holding a
+// register; completion is awaited per thread with wait_group and published to the block with a
+// barrier.
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Issues the AA-pattern gather of one cell as asynchronous copies into buf[i * stride].
+template <int Q, int PARITY, bool SOLIDS>
+__device__ __forceinline__ void gather32_async(const KParams& kp, const Off32& o, uint32_t bits, float* buf,
+                                               int stride) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float* src;
+        if (PARITY == 0 || i == 0) src = kp.fq[i] + o.c;
+        else if (SOLIDS && ((bits >> OPP(i)) & 1u)) src = kp.fq[i] + o.c;
+        else src = kp.fq[OPP(i)] + o.nb(-EX(i), -EY(i), -EZ(i));
+        cp_async4(buf + i * stride, src);
+    }
+}
+
 // Forces from three psi planes (z-1, z, z+1); each pointer addresses psi(x) within its plane,
 // x stride 1 and y stride sy.
 template <int Q, bool SOLIDS>
