@@ -61,6 +61,32 @@ constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
 constexpr int ZM_NT = ZM_BX * ZM_BY;
 constexpr int ZM_SLOTS = (ZM_RP + ZM_NT - 1) / ZM_NT;  // psi loads per thread per plane
 
+// psi plane zz (wrapped, or zeros beyond a wall) into one ring slot; each thread copies its
+// ZM_SLOTS entries, whose x/y offsets are fixed for the whole march.
+__device__ __forceinline__ void load_psi_plane(float* slot, const float* __restrict__ psi, int zz, int nz, int wall_z,
+                                               uint32_t nxy, const uint32_t (&goff)[ZM_SLOTS],
+                                               const bool (&gok)[ZM_SLOTS], int tid) {
+    bool zok = true;
+    if (zz < 0) { zok = !wall_z; zz += nz; } else if (zz >= nz) { zok = !wall_z; zz -= nz; }
+    const uint32_t zb = (uint32_t)zz * nxy;
+#pragma unroll
+    for (int s = 0; s < ZM_SLOTS; ++s) {
+        const int k = tid + s * ZM_NT;
+        if (k < ZM_RP) {
+            if (zok && gok[s]) cp_async4(&slot[k], psi + zb + goff[s]);
+            else slot[k] = 0.0f;
+        }
+    }
+}
+
+// plane offsets of z in a 32-bit neighbourhood
+__device__ __forceinline__ void set_plane(Off32& o, int z, int nz, uint32_t nxy) {
+    o.zo[0] = (uint32_t)wrap1(z - 1, nz) * nxy;
+    o.zo[1] = (uint32_t)z * nxy;
+    o.zo[2] = (uint32_t)wrap1(z + 1, nz) * nxy;
+    o.c = o.zo[1] + o.yo[1] + o.xo[1];
+}
+
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
 __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
                                                                 const uint32_t* __restrict__ nbmask,
@@ -71,12 +97,12 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x0 = blockIdx.x * ZM_BX, y0 = blockIdx.y * ZM_BY, z0 = blockIdx.z * zchunk;
     const int x = x0 + tx, y = y0 + ty;
-    const bool act_xy = x < kp.nx && y < kp.ny;
-    const uint32_t nxy = (uint32_t)kp.nx * (uint32_t)kp.ny;
-    const int zend = min(z0 + zchunk, kp.nz);
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const bool act_xy = x < nx && y < ny;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    const int zend = min(z0 + zchunk, nz);
     const int nplanes = zend - z0;
 
-    // this thread's share of each psi plane (x/y offsets fixed for the whole march)
     uint32_t goff[ZM_SLOTS];
     bool gok[ZM_SLOTS];
 #pragma unroll
@@ -84,55 +110,31 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
         const int k = tid + s * ZM_NT;
         int gx = x0 - 1 + k % ZM_RX, gy = y0 - 1 + k / ZM_RX;
         bool ok = k < ZM_RP;
-        if (gx < 0) { ok &= !kp.wall_x; gx += kp.nx; } else if (gx >= kp.nx) { ok &= !kp.wall_x; gx -= kp.nx; }
-        if (gy < 0) { ok &= !kp.wall_y; gy += kp.ny; } else if (gy >= kp.ny) { ok &= !kp.wall_y; gy -= kp.ny; }
-        ok = ok && gx >= 0 && gx < kp.nx && gy >= 0 && gy < kp.ny;
+        if (gx < 0) { ok &= !kp.wall_x; gx += nx; } else if (gx >= nx) { ok &= !kp.wall_x; gx -= nx; }
+        if (gy < 0) { ok &= !kp.wall_y; gy += ny; } else if (gy >= ny) { ok &= !kp.wall_y; gy -= ny; }
+        ok = ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         gok[s] = ok;
-        goff[s] = ok ? (uint32_t)gy * (uint32_t)kp.nx + (uint32_t)gx : 0u;
+        goff[s] = ok ? (uint32_t)gy * (uint32_t)nx + (uint32_t)gx : 0u;
     }
-    // psi plane zz (wrapped, or zeros beyond a wall) into ring slot `slot`
-    auto load_plane = [&](int zz, int slot) {
-        bool zok = true;
-        if (zz < 0) { zok = !kp.wall_z; zz += kp.nz; } else if (zz >= kp.nz) { zok = !kp.wall_z; zz -= kp.nz; }
-        const uint32_t zb = (uint32_t)zz * nxy;
-#pragma unroll
-        for (int s = 0; s < ZM_SLOTS; ++s) {
-            const int k = tid + s * ZM_NT;
-            if (k < ZM_RP) {
-                if (zok && gok[s]) cp_async4(&ring[slot][k], psi + zb + goff[s]);
-                else ring[slot][k] = 0.0f;
-            }
-        }
-    };
 
     Off32 o;
-    o.xo[0] = (uint32_t)wrap1(x - 1, kp.nx);
+    o.xo[0] = (uint32_t)wrap1(x - 1, nx);
     o.xo[1] = (uint32_t)x;
-    o.xo[2] = (uint32_t)wrap1(x + 1, kp.nx);
-    o.yo[0] = (uint32_t)wrap1(y - 1, kp.ny) * (uint32_t)kp.nx;
-    o.yo[1] = (uint32_t)y * (uint32_t)kp.nx;
-    o.yo[2] = (uint32_t)wrap1(y + 1, kp.ny) * (uint32_t)kp.nx;
-    auto set_plane = [&](int z) {
-        o.zo[0] = (uint32_t)wrap1(z - 1, kp.nz) * nxy;
-        o.zo[1] = (uint32_t)z * nxy;
-        o.zo[2] = (uint32_t)wrap1(z + 1, kp.nz) * nxy;
-        o.c = o.zo[1] + o.yo[1] + o.xo[1];
-    };
-    // solid bits of plane z (interior solids from nbmask, walls from the position)
-    auto plane_bits = [&](int z) -> uint32_t {
-        return SOLIDS ? solid_bits32<Q>(kp, nbmask, o.zo[1] + o.yo[1] + o.xo[1], x, y, z) : 0u;
-    };
+    o.xo[2] = (uint32_t)wrap1(x + 1, nx);
+    o.yo[0] = (uint32_t)wrap1(y - 1, ny) * (uint32_t)nx;
+    o.yo[1] = (uint32_t)y * (uint32_t)nx;
+    o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
 
     // prologue: psi planes z0-1, z0, z0+1 and the populations of plane z0
     uint32_t bits_cur = 0u;
     if (MULTIPHASE) {
-        load_plane(z0 - 1, 0);
-        load_plane(z0, 1);
-        load_plane(z0 + 1, 2);
+        load_psi_plane(ring[0], psi, z0 - 1, nz, kp.wall_z, nxy, goff, gok, tid);
+        load_psi_plane(ring[1], psi, z0, nz, kp.wall_z, nxy, goff, gok, tid);
+        load_psi_plane(ring[2], psi, z0 + 1, nz, kp.wall_z, nxy, goff, gok, tid);
     }
     if (act_xy) {
-        set_plane(z0);
-        bits_cur = plane_bits(z0);
+        set_plane(o, z0, nz, nxy);
+        bits_cur = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z0) : 0u;
         if (!(bits_cur & 1u)) gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_cur, &pops[0][0][tid], ZM_NT);
     }
     cp_async_commit();
@@ -144,17 +146,17 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
         // prefetch plane z+1 (populations) and psi plane z+2 while plane z is computed
         uint32_t bits_next = 0u;
         if (j + 1 < nplanes) {
-            if (MULTIPHASE) load_plane(z + 2, (j + 3) & 3);
+            if (MULTIPHASE) load_psi_plane(ring[(j + 3) & 3], psi, z + 2, nz, kp.wall_z, nxy, goff, gok, tid);
             if (act_xy) {
-                set_plane(z + 1);
-                bits_next = plane_bits(z + 1);
+                set_plane(o, z + 1, nz, nxy);
+                bits_next = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z + 1) : 0u;
                 if (!(bits_next & 1u))
                     gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_next, &pops[(j + 1) & 1][0][tid], ZM_NT);
             }
         }
         cp_async_commit();
         if (act_xy && !(bits_cur & 1u)) {
-            set_plane(z);
+            set_plane(o, z, nz, nxy);
             float p[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) p[i] = pops[j & 1][i][tid];
@@ -339,6 +341,24 @@ dim3 cs_grid(const KParams& kp) {
     return dim3((kp.nx + CS_BX - 1) / CS_BX, (kp.ny + CS_BY - 1) / CS_BY, (kp.nz + CS_BZ - 1) / CS_BZ);
 }
 
+// Launches one collide_kernel instantiation; the first launch asks for the largest shared-memory
+// carveout so that ZM_MINB blocks (with their population stages) fit on an SM.
+// (internal linkage: each lattice's translation unit must launch its own kernels)
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const float* psi,
+                                   const uint32_t* nbmask, unsigned* status, int zc) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    collide_kernel<PARITY, SOLIDS, MULTIPHASE><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define LBM_CAT2(a, b) a##b
@@ -362,23 +382,6 @@ static int collide_zchunk(const KParams& kp) {
     if (chunks > kp.nz) chunks = kp.nz;
     if (chunks < 1) chunks = 1;
     return (int)((kp.nz + chunks - 1) / chunks);
-}
-
-// Launches one collide_kernel instantiation; the first launch asks for the largest shared-memory
-// carveout so that ZM_MINB blocks (with their population stages) fit on an SM.
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const float* psi,
-                                   const uint32_t* nbmask, unsigned* status, int zc) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
-                                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    collide_kernel<PARITY, SOLIDS, MULTIPHASE><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc);
-    return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, float* f, const float* psi,

@@ -13,6 +13,7 @@
 // f*_i -> slot ibar of x); an even step is local and needs no test.
 #pragma once
 
+#include <cuda_pipeline.h>
 #include <stdint.h>
 
 #include "lbm_internal.h"
@@ -358,15 +359,14 @@ __device__ __forceinline__ void store32(const KParams& kp, const Off32& o, uint3
 }
 
 // ------------------------------------------------------------------ asynchronous global -> shared copies
-// cp.async (4-byte form, any 4-byte-aligned address): the copy is in flight without holding a
-// register; completion is awaited per thread with wait_group and published to the block with a
-// barrier.
+// 4-byte asynchronous copies (cp.async through the CUDA pipeline primitives): the copy is in
+// flight without holding a register; completion is awaited per thread and published to the
+// block with a barrier.
 __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    __pipeline_memcpy_async(smem_dst, gsrc, sizeof(float));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { __pipeline_commit(); }
+__device__ __forceinline__ void cp_async_wait_all() { __pipeline_wait_prior(0); }
 
 // Issues the AA-pattern gather of one cell as asynchronous copies into buf[i * stride].
 template <int Q, int PARITY, bool SOLIDS>

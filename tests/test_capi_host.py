@@ -71,3 +71,19 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.lbm_step_count(None) == -1
     lib.lbm_destroy(None)
     assert lib.lbm_status_string(4) == b"LBM_ERR_UNSTABLE"
+
+
+def test_per_lattice_launch_helpers_have_internal_linkage(lib):
+    # The D3Q19 and D3Q27 kernels are compiled from one source in two translation units; any
+    # helper that names a per-lattice kernel must stay local, or the linker folds the two copies
+    # into one and one lattice launches the other's kernels.
+    import shutil
+    import subprocess
+    if not shutil.which("nm"):
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-C", L.LIB_PATH], capture_output=True, text=True).stdout
+    rows = [r for r in out.splitlines() if "launch_collide_variant" in r or "collide_kernel" in r]
+    assert rows
+    for r in rows:
+        kind = r.split()[1] if len(r.split()) > 2 else r.split()[0]
+        assert kind in ("t", "d", "b", "r"), r
