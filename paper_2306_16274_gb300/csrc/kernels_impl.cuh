@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
 // Tiles of 32 x ZM_BY cells in (x, y) march through a chunk of z planes.  psi planes
 // z-1, z, z+1 (with a one-cell x/y halo) sit in a four-slot shared-memory ring, so
-// each plane is read once per tile.  The populations of plane z+1 (AA gather) and
-// psi plane z+2 are fetched with cp.async into shared memory while plane z is being
-// computed; one barrier per plane orders the copies and the ring reuse.
+// each plane is read once per tile and one barrier per plane suffices.  (Staging the
+// populations through shared memory with cp.async measured slower: it doubles the
+// load/store instructions of an issue-bound kernel.)
 constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
 // tile height and blocks per SM (register cap 64 for D3Q19, 85 for D3Q27): best of a
 // measured sweep of (8, 4, 3), (8, 3, 2), (4, 8, 6), (8, 5, 4) on 256^3
@@ -61,7 +61,15 @@ constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
 constexpr int ZM_NT = ZM_BX * ZM_BY;
 constexpr int ZM_SLOTS = (ZM_RP + ZM_NT - 1) / ZM_NT;  // psi loads per thread per plane
 
-// psi plane zz (wrapped, or zeros beyond a wall) into one ring slot; each thread copies its
+// plane offsets of z in a 32-bit neighbourhood
+__device__ __forceinline__ void set_plane(Off32& o, int z, int nz, uint32_t nxy) {
+    o.zo[0] = (uint32_t)wrap1(z - 1, nz) * nxy;
+    o.zo[1] = (uint32_t)z * nxy;
+    o.zo[2] = (uint32_t)wrap1(z + 1, nz) * nxy;
+    o.c = o.zo[1] + o.yo[1] + o.xo[1];
+}
+
+// psi plane zz (wrapped, or zeros beyond a wall) into one ring slot; each thread loads its
 // ZM_SLOTS entries, whose x/y offsets are fixed for the whole march.
 __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restrict__ psi, int zz, int nz, int wall_z,
                                                uint32_t nxy, const uint32_t (&goff)[ZM_SLOTS],
@@ -72,28 +80,19 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 #pragma unroll
     for (int s = 0; s < ZM_SLOTS; ++s) {
         const int k = tid + s * ZM_NT;
-        if (k < ZM_RP) {
-            if (zok && gok[s]) cp_async4(&slot[k], psi + zb + goff[s]);
-            else slot[k] = 0.0f;
-        }
+        if (k < ZM_RP) slot[k] = (zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
     }
 }
 
-// plane offsets of z in a 32-bit neighbourhood
-__device__ __forceinline__ void set_plane(Off32& o, int z, int nz, uint32_t nxy) {
-    o.zo[0] = (uint32_t)wrap1(z - 1, nz) * nxy;
-    o.zo[1] = (uint32_t)z * nxy;
-    o.zo[2] = (uint32_t)wrap1(z + 1, nz) * nxy;
-    o.c = o.zo[1] + o.yo[1] + o.xo[1];
-}
+#ifndef LBM_ZM_PREFETCH
+#define LBM_ZM_PREFETCH 0
+#endif
 
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
 __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
                                                                 const uint32_t* __restrict__ nbmask,
                                                                 unsigned* status, int zchunk) {
-    // ring: psi planes (4 slots); pops: two stages of this block's populations, [stage][i][thread]
     __shared__ float ring[4][ZM_RP];
-    __shared__ float pops[2][Q][ZM_NT];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x0 = blockIdx.x * ZM_BX, y0 = blockIdx.y * ZM_BY, z0 = blockIdx.z * zchunk;
     const int x = x0 + tx, y = y0 + ty;
@@ -101,7 +100,6 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     const bool act_xy = x < nx && y < ny;
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
     const int zend = min(z0 + zchunk, nz);
-    const int nplanes = zend - z0;
 
     uint32_t goff[ZM_SLOTS];
     bool gok[ZM_SLOTS];
@@ -125,59 +123,60 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     o.yo[1] = (uint32_t)y * (uint32_t)nx;
     o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
 
-    // prologue: psi planes z0-1, z0, z0+1 and the populations of plane z0
-    uint32_t bits_cur = 0u;
     if (MULTIPHASE) {
         load_psi_plane(ring[0], psi, z0 - 1, nz, kp.wall_z, nxy, goff, gok, tid);
         load_psi_plane(ring[1], psi, z0, nz, kp.wall_z, nxy, goff, gok, tid);
-        load_psi_plane(ring[2], psi, z0 + 1, nz, kp.wall_z, nxy, goff, gok, tid);
     }
+#if LBM_ZM_PREFETCH
+    // populations of the first plane, then of plane z+1 while plane z is computed
+    float pn[Q];
+    uint32_t bits_n = 0u;
     if (act_xy) {
         set_plane(o, z0, nz, nxy);
-        bits_cur = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z0) : 0u;
-        if (!(bits_cur & 1u)) gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_cur, &pops[0][0][tid], ZM_NT);
+        bits_n = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z0) : 0u;
+        if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(kp, o, bits_n, pn);
     }
-    cp_async_commit();
-
-    for (int j = 0; j < nplanes; ++j) {
-        const int z = z0 + j;
-        cp_async_wait_all();   // this thread's copies for plane z (and psi plane z+1)
-        __syncthreads();       // everyone's copies visible; everyone finished plane z-1
-        // prefetch plane z+1 (populations) and psi plane z+2 while plane z is computed
-        uint32_t bits_next = 0u;
-        if (j + 1 < nplanes) {
-            if (MULTIPHASE) load_psi_plane(ring[(j + 3) & 3], psi, z + 2, nz, kp.wall_z, nxy, goff, gok, tid);
-            if (act_xy) {
-                set_plane(o, z + 1, nz, nxy);
-                bits_next = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z + 1) : 0u;
-                if (!(bits_next & 1u))
-                    gather32_async<Q, PARITY, SOLIDS>(kp, o, bits_next, &pops[(j + 1) & 1][0][tid], ZM_NT);
-            }
+#endif
+    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
+    for (int z = z0, j = 0; z < zend; ++z, ++j) {
+        if (MULTIPHASE) {
+            load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, kp.wall_z, nxy, goff, gok, tid);
+            __syncthreads();
         }
-        cp_async_commit();
-        if (act_xy && !(bits_cur & 1u)) {
-            set_plane(o, z, nz, nxy);
-            float p[Q];
+        if (!act_xy) continue;
+#if LBM_ZM_PREFETCH
+        float p[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) p[i] = pops[j & 1][i][tid];
-            Forces Fo;
-            if (MULTIPHASE) {
-                const int lc = (ty + 1) * ZM_RX + tx + 1;
-                Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
-                                                ZM_RX, bits_cur);
-            } else {
-                Fo.fx = Fo.fy = Fo.fz = 0.f;
-                Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
-                Fo.s2 = 0.f;
-            }
-            float rho, ux, uy, uz;
-            collide<Q>(kp, p, Fo, rho, ux, uy, uz);
-            if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
-            store32<Q, PARITY, SOLIDS>(kp, o, bits_cur, p);
+        for (int i = 0; i < Q; ++i) p[i] = pn[i];
+        const uint32_t bits = bits_n;
+        if (z + 1 < zend) {
+            set_plane(o, z + 1, nz, nxy);
+            bits_n = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z + 1) : 0u;
+            if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(kp, o, bits_n, pn);
         }
-        bits_cur = bits_next;
+        set_plane(o, z, nz, nxy);
+        if (bits & 1u) continue;
+#else
+        set_plane(o, z, nz, nxy);
+        const uint32_t bits = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z) : 0u;
+        if (bits & 1u) continue;
+        float p[Q];
+        gather32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+#endif
+        Forces Fo;
+        if (MULTIPHASE) {
+            Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
+                                            ZM_RX, bits);
+        } else {
+            Fo.fx = Fo.fy = Fo.fz = 0.f;
+            Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+            Fo.s2 = 0.f;
+        }
+        float rho, ux, uy, uz;
+        collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+        if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+        store32<Q, PARITY, SOLIDS>(kp, o, bits, p);
     }
-    cp_async_wait_all();
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout

@@ -13,7 +13,6 @@
 // f*_i -> slot ibar of x); an even step is local and needs no test.
 #pragma once
 
-#include <cuda_pipeline.h>
 #include <stdint.h>
 
 #include "lbm_internal.h"
@@ -355,30 +354,6 @@ __device__ __forceinline__ void store32(const KParams& kp, const Off32& o, uint3
         } else {
             kp.fq[i][o.nb(EX(i), EY(i), EZ(i))] = p[i];
         }
-    }
-}
-
-// ------------------------------------------------------------------ asynchronous global -> shared copies
-// 4-byte asynchronous copies (cp.async through the CUDA pipeline primitives): the copy is in
-// flight without holding a register; completion is awaited per thread and published to the
-// block with a barrier.
-__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
-    __pipeline_memcpy_async(smem_dst, gsrc, sizeof(float));
-}
-__device__ __forceinline__ void cp_async_commit() { __pipeline_commit(); }
-__device__ __forceinline__ void cp_async_wait_all() { __pipeline_wait_prior(0); }
-
-// Issues the AA-pattern gather of one cell as asynchronous copies into buf[i * stride].
-template <int Q, int PARITY, bool SOLIDS>
-__device__ __forceinline__ void gather32_async(const KParams& kp, const Off32& o, uint32_t bits, float* buf,
-                                               int stride) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float* src;
-        if (PARITY == 0 || i == 0) src = kp.fq[i] + o.c;
-        else if (SOLIDS && ((bits >> OPP(i)) & 1u)) src = kp.fq[i] + o.c;
-        else src = kp.fq[OPP(i)] + o.nb(-EX(i), -EY(i), -EZ(i));
-        cp_async4(buf + i * stride, src);
     }
 }
 
