@@ -45,16 +45,17 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 // populations through shared memory with cp.async measured slower: it doubles the
 // load/store instructions of an issue-bound kernel.)
 constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
-// tile height and blocks per SM (register cap 64 for D3Q19, 85 for D3Q27): best of a
-// measured sweep of (8, 4, 3), (8, 3, 2), (4, 8, 6), (8, 5, 4) on 256^3
+// tile height and blocks per SM (register caps 85 for D3Q19, 102 for D3Q27), with the next
+// plane's populations prefetched into registers: the best of measured sweeps over tile
+// height 2/4/8, 3-16 blocks per SM, prefetch on/off and the shared-memory carveout on 256^3
 #ifndef LBM_ZM_BY
 #define LBM_ZM_BY 4
 #endif
 #ifndef LBM_ZM_MINB19
-#define LBM_ZM_MINB19 8
+#define LBM_ZM_MINB19 6
 #endif
 #ifndef LBM_ZM_MINB27
-#define LBM_ZM_MINB27 6
+#define LBM_ZM_MINB27 5
 #endif
 constexpr int ZM_BX = 32, ZM_BY = LBM_ZM_BY, ZM_MINB = LBM_Q == 19 ? LBM_ZM_MINB19 : LBM_ZM_MINB27;
 constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
@@ -85,7 +86,7 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 }
 
 #ifndef LBM_ZM_PREFETCH
-#define LBM_ZM_PREFETCH 0
+#define LBM_ZM_PREFETCH 1
 #endif
 
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
@@ -340,19 +341,24 @@ dim3 cs_grid(const KParams& kp) {
     return dim3((kp.nx + CS_BX - 1) / CS_BX, (kp.ny + CS_BY - 1) / CS_BY, (kp.nz + CS_BZ - 1) / CS_BZ);
 }
 
-// Launches one collide_kernel instantiation; the first launch asks for the largest shared-memory
-// carveout so that ZM_MINB blocks (with their population stages) fit on an SM.
-// (internal linkage: each lattice's translation unit must launch its own kernels)
+// Launches one collide_kernel instantiation (internal linkage: each lattice's translation unit
+// must launch its own kernels).  LBM_ZM_CARVEOUT >= 0 sets the preferred shared-memory carveout
+// (percent) once; the default leaves the driver's choice, which keeps L1 large for the
+// neighbour and psi-halo loads.
+#ifndef LBM_ZM_CARVEOUT
+#define LBM_ZM_CARVEOUT -1
+#endif
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
 cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const float* psi,
                                    const uint32_t* nbmask, unsigned* status, int zc) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
-                                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
+    if (LBM_ZM_CARVEOUT >= 0) {
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
+                                                 cudaFuncAttributePreferredSharedMemoryCarveout, LBM_ZM_CARVEOUT);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
     }
     collide_kernel<PARITY, SOLIDS, MULTIPHASE><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc);
     return cudaGetLastError();
