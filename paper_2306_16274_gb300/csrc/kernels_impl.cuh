@@ -45,14 +45,14 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
 // populations through shared memory with cp.async measured slower: it doubles the
 // load/store instructions of an issue-bound kernel.)
 constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the moments kernel
-// tile height and blocks per SM (register caps 85 for D3Q19, 102 for D3Q27), with the next
+// tile height and blocks per SM (register caps 73 for D3Q19, 102 for D3Q27), with the next
 // plane's populations prefetched into registers: the best of measured sweeps over tile
 // height 2/4/8, 3-16 blocks per SM, prefetch on/off and the shared-memory carveout on 256^3
 #ifndef LBM_ZM_BY
 #define LBM_ZM_BY 4
 #endif
 #ifndef LBM_ZM_MINB19
-#define LBM_ZM_MINB19 6
+#define LBM_ZM_MINB19 7
 #endif
 #ifndef LBM_ZM_MINB27
 #define LBM_ZM_MINB27 5
