@@ -98,11 +98,14 @@ typedef struct {
     double psi_fp64_rho;    /* C-S only: cells with rho >= this evaluate p_EOS - rho c_s^2   */
                             /* in FP64 (liquid branch); a negative value selects the default */
                             /* b * rho_c = 0.52177 (critical density); +inf: never           */
+    int32_t zchunk;         /* tuning: z planes one collide block marches through; 0 = chosen */
+                            /* from the domain size (results do not depend on it)            */
 } lbm_params;
 
 /* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,
  * s0 = s1 = 1, s2b = s3b = 0.6, others 1.2 (text after Eq. e12), sigma = 0.1
- * (Sec. III A), everything else 0, psi_fp64_rho = -1 (default threshold). */
+ * (Sec. III A), everything else 0, psi_fp64_rho = -1 (default threshold),
+ * zchunk = 0 (automatic). */
 void lbm_default_params(lbm_params* p);
 
 /* Validates *params, allocates the device state on the current device and

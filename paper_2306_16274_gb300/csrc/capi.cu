@@ -88,6 +88,7 @@ lbm_status validate(const lbm_params* p, std::string& why) {
             return LBM_ERR_ARG;
         }
     }
+    if (p->zchunk < 0) { why = "zchunk must be >= 0"; return LBM_ERR_ARG; }
     if (p->variable_nu) {
         if (!(p->rho_l != p->rho_v) || !(p->nu_l > 0.0) || !(p->nu_v > 0.0)) {
             why = "variable viscosity needs rho_l != rho_v and nu_l, nu_v > 0";
@@ -156,6 +157,7 @@ KParams derive(const lbm_params& p, long long plane) {
     k.gx = (float)p.g[0];
     k.gy = (float)p.g[1];
     k.gz = (float)p.g[2];
+    k.zchunk = p.zchunk;
     return k;
 }
 

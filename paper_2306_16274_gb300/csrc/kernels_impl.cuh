@@ -381,6 +381,7 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
 
 // z planes per block: enough blocks for a few waves of resident blocks on 152 SMs
 static int collide_zchunk(const KParams& kp) {
+    if (kp.zchunk > 0) return kp.zchunk < kp.nz ? kp.zchunk : kp.nz;
     const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + ZM_BY - 1) / ZM_BY);
     const long long target = 152LL * ZM_MINB * 4;
     long long chunks = (target + cols - 1) / cols;

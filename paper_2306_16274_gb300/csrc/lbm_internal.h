@@ -39,6 +39,7 @@ struct KParams {
     float nu_v, dnu_drho, rho_v;  // nu(rho) = nu_v + dnu_drho (rho - rho_v)
     float gx, gy, gz;             // body force per unit mass
     float* fq[27];                // base of population plane i (f + i * plane); cells < 2^31
+    int zchunk;                   // z planes per collide block (0 = automatic)
 };
 
 // Launchers (one set per lattice).  parity: 0 = natural layout (even AA step),

@@ -36,7 +36,7 @@ class lbm_params(ctypes.Structure):
         ("G", ctypes.c_double), ("G_ads", ctypes.c_double), ("kappa", ctypes.c_double), ("sigma", ctypes.c_double),
         ("s", ctypes.c_double * 10), ("variable_nu", ctypes.c_int32),
         ("nu_l", ctypes.c_double), ("nu_v", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
-        ("g", ctypes.c_double * 3), ("psi_fp64_rho", ctypes.c_double),
+        ("g", ctypes.c_double * 3), ("psi_fp64_rho", ctypes.c_double), ("zchunk", ctypes.c_int32),
     ]
 
 
@@ -103,6 +103,7 @@ class Params:
     rho_v: float = 0.0
     g: tuple = (0.0, 0.0, 0.0)
     psi_fp64_rho: float = -1.0
+    zchunk: int = 0
 
     def to_c(self):
         c = lbm_params()
@@ -124,6 +125,7 @@ class Params:
         for k in range(3):
             c.g[k] = float(self.g[k])
         c.psi_fp64_rho = float(self.psi_fp64_rho)
+        c.zchunk = int(self.zchunk)
         return c
 
     @property

@@ -1,0 +1,84 @@
+"""Full-size checks in the launch configuration bench.py times: the 256^3 at-scale workload with
+automatic z-chunks (each collide block marches through ~29 planes).  Sampled cells are compared
+with the oracle, which advances a small periodic sub-box around each sample: after one step a
+cell depends only on the initial state within two cells (psi stencil of its pull sources), after
+two steps within four, so a sub-box of radius 3 / 5 reproduces the full-domain result at its
+centre.  Conservation is checked over the whole domain."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import lbm as olbm
+from tests import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (256, 256, 256)
+
+
+@pytest.fixture(scope="module")
+def workload():
+    import __graft_entry__
+    __graft_entry__.build()
+    rho, u, wparams = bench.workload_fields(SHAPE)
+    return rho, u, wparams
+
+
+def _samples(rho, seed, n_interface=8, n_other=4):
+    rng = np.random.default_rng(seed)
+    lo, hi = rho.min(), rho.max()
+    frac = (rho - lo) / (hi - lo)
+    iface = np.argwhere((frac > 0.1) & (frac < 0.9))
+    pick = iface[rng.choice(len(iface), n_interface, replace=False)]
+    other = rng.integers(0, 256, size=(n_other, 3))
+    edges = np.array([[0, 0, 0], [255, 255, 255], [0, 128, 255], [255, 7, 0]])   # periodic wrap in z, y, x
+    return np.concatenate([pick, other, edges])
+
+
+def _oracle_subbox(d, rho, u, center, radius, steps):
+    z, y, x = (int(c) for c in center)
+    idx = [np.arange(c - radius, c + radius + 1) % 256 for c in (z, y, x)]
+    r = rho[np.ix_(*idx)]
+    uu = u[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+    n = 2 * radius + 1
+    dd = dict(d)
+    dd["shape"] = (n, n, n)
+    s = U.run_oracle(dd, r, uu, steps=steps)
+    return s.f[:, radius, radius, radius]
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("steps", [1, 2])
+def test_sampled_cells_match_oracle(workload, Q, steps):
+    import torch
+    rho, u, wparams = workload
+    d = dict(lattice=Q, shape=SHAPE, **wparams)
+    sim = U.run_gpu(d, rho, u, steps=steps)
+    f = sim.populations()
+    samples = _samples(rho, seed=Q * 10 + steps)
+    idx = torch.tensor(samples, device=f.device, dtype=torch.long)
+    fg = f[:, idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    del f
+    sim.close()
+    torch.cuda.empty_cache()
+    radius = 3 if steps == 1 else 5
+    for k, c in enumerate(samples):
+        fo = _oracle_subbox(d, rho, u, c, radius, steps)
+        err = np.abs(fg[:, k] - fo).max()
+        assert err < 2e-6 * np.abs(fo).max(), (tuple(c), err)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_fullsize_conservation(workload, Q):
+    # total mass (and total momentum, F_int being pairwise antisymmetric) is invariant on the
+    # periodic box; FP32 populations drift only by rounding
+    rho, u, wparams = workload
+    d = dict(lattice=Q, shape=SHAPE, **wparams)
+    sim = U.run_gpu(d, rho, u, steps=0)
+    _, _, s0 = sim.moments()
+    sim.step(200)
+    sim.sync()
+    _, _, s1 = sim.moments()
+    sim.close()
+    assert abs(s1[0] - s0[0]) < 1e-5 * s0[0]
+    assert np.abs(s1[1:] - s0[1:]).max() < 1e-5 * s0[0]

@@ -27,8 +27,10 @@ SHAPES = [(37, 13, 9), (20, 9, 7)]
 
 @pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_single_phase_periodic(Q, shape):
-    d = dict(lattice=Q, shape=shape, rates={"s2": 1.3, "s3": 1.1, "s5": 1.4, "s6": 0.9})
+@pytest.mark.parametrize("zchunk", [0, 3])
+def test_single_phase_periodic(Q, shape, zchunk):
+    # zchunk 3: every collide block marches through several z planes (next-plane prefetch path)
+    d = dict(lattice=Q, shape=shape, rates={"s2": 1.3, "s3": 1.1, "s5": 1.4, "s6": 0.9}, zchunk=zchunk)
     rho, u = W.perturbed(shape, seed=3)
     sim = U.run_gpu(d, rho, u, steps=100)
     ref = U.run_oracle(d, rho, u, steps=100)
@@ -42,7 +44,7 @@ def test_single_phase_periodic(Q, shape):
 def test_populations_every_parity(Q, steps):
     # element-wise populations after odd and even step counts (AA layout converted back)
     shape = (35, 6, 5)
-    d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), g=(1e-5, 0.0, -2e-5))
+    d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), g=(1e-5, 0.0, -2e-5), zchunk=2)
     rho, u = W.perturbed(shape, seed=5)
     solid = W.random_mask(shape, 0.08, seed=9)
     sim = U.run_gpu(d, rho, u, solid, steps=steps)
@@ -56,7 +58,7 @@ def test_populations_every_parity(Q, steps):
 @pytest.mark.parametrize("Q", [19, 27])
 def test_walls_solids_body_force(Q):
     shape = (33, 10, 12)
-    d = dict(lattice=Q, shape=shape, bc=(0, 1, 1), g=(2e-5, 0.0, 0.0), rates={"s2": 0.9})
+    d = dict(lattice=Q, shape=shape, bc=(0, 1, 1), g=(2e-5, 0.0, 0.0), rates={"s2": 0.9}, zchunk=5)
     rho, u = W.perturbed(shape, seed=7, U=0.02)
     solid = W.random_mask(shape, 0.05, seed=1)
     sim = U.run_gpu(d, rho, u, solid, steps=100)
@@ -82,11 +84,12 @@ def test_psi_after_init(Q):
 
 
 @pytest.mark.parametrize("Q", [19, 27])
-def test_static_droplet_laplace_config(Q):
+@pytest.mark.parametrize("zchunk", [0, 7])
+def test_static_droplet_laplace_config(Q, zchunk):
     # 32^3 periodic, C-S at 0.7 T_c, droplet R = 8 with the tanh profile (W = 2), kappa = 0
     shape = (32, 32, 32)
     kw, rl, rv = U.cs_eos("T0.7")
-    d = dict(lattice=Q, shape=shape, sigma=0.1, **kw)
+    d = dict(lattice=Q, shape=shape, sigma=0.1, zchunk=zchunk, **kw)
     rho, u = W.droplet(shape, 8.0, rl, rv)
     sim = U.run_gpu(d, rho, u, steps=100)
     ref = U.run_oracle(d, rho, u, steps=100)
@@ -104,10 +107,10 @@ def test_many_droplets_large_density_ratio(Q, case):
     shape = (40, 36, 28)
     if case == "T0.5_kappa0_paper_rates":
         kw, rl, rv = U.cs_eos("T0.5")
-        d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.0, **kw)
+        d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.0, zchunk=4, **kw)
     else:
         kw, rl, rv = U.cs_eos("T0.55")
-        d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.5, rates={"s2b": 1.0}, **kw)
+        d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.5, rates={"s2b": 1.0}, zchunk=4, **kw)
     rho, u, _ = W.random_spheres(shape, rl, rv, 4.0, 8.0, seed=2306, target_fraction=0.10, gap=4.0, W=5.0)
     sim = U.run_gpu(d, rho, u, steps=100)
     ref = U.run_oracle(d, rho, u, steps=100)
@@ -122,7 +125,7 @@ def test_impact_walls_wetting_variable_viscosity(Q):
     shape = (36, 34, 22)
     kw, rl, rv = U.pw_eos()
     d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), sigma=0.1, kappa=0.3, G_ads=-0.05,
-             variable_nu=True, nu_l=0.02, nu_v=0.1, rho_l=rl, rho_v=rv, g=(0.0, 0.0, -1e-6), **kw)
+             variable_nu=True, nu_l=0.02, nu_v=0.1, rho_l=rl, rho_v=rv, g=(0.0, 0.0, -1e-6), zchunk=6, **kw)
     rho, u = W.impact(shape, 7.0, rl, rv, U=0.05, gap=3.0)
     sim = U.run_gpu(d, rho, u, steps=100)
     ref = U.run_oracle(d, rho, u, steps=100)
