@@ -239,6 +239,94 @@ def run_e2e(Q, rho, u, wparams, steps):
                 d2h_bytes_per_step=d2h / steps, seconds=t1 - t0)
 
 
+# ---------------------------------------------------------------- batched jobs
+BATCH_WORKLOAD = ("64 independent jobs, cubic edge L ~ U{48..160} (numpy seed 2306), lattice D3Q19/D3Q27 and job "
+                  "type by fair coin: static droplet (periodic, R = L/4) or droplet impact on a flat wall (walls in z, "
+                  "R = L/5, 3 cells above the wall, U = 0.02), C-S at 0.7 T_c, sigma = 0.1, kappa = 0.3, FP32")
+
+
+def batch_jobs(n_jobs=64, seed=2306):
+    c = W.constants()["cs"]
+    t = c["T0.7"]
+    eos = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1, kappa=0.3)
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(n_jobs):
+        L = int(rng.integers(48, 161))
+        Q = 19 if rng.random() < 0.5 else 27
+        impact = rng.random() < 0.5
+        if impact:
+            rho, u = W.impact((L, L, L), L / 5.0, t["rho_l"], t["rho_v"], U=0.02, gap=3.0)
+            params = dict(lattice=Q, shape=(L, L, L), bc=("periodic", "periodic", "wall"), **eos)
+        else:
+            rho, u = W.droplet((L, L, L), L / 4.0, t["rho_l"], t["rho_v"])
+            params = dict(lattice=Q, shape=(L, L, L), **eos)
+        jobs.append((params, rho, u))
+    return jobs
+
+
+def run_batched(steps, n_jobs=64):
+    """The same jobs advanced one at a time (each job's `steps` steps through the plain single-domain
+    kernels, jobs back to back) and together (one tuned batch, one graph launch)."""
+    import torch
+
+    from paper_2306_16274_gb300 import Batch, Params, Simulation
+    jobs = batch_jobs(n_jobs)
+    stream = torch.cuda.Stream()
+    sims, inputs = [], []
+    with torch.cuda.stream(stream):
+        for params, rho, u in jobs:
+            sims.append(Simulation(Params(**params), stream=stream))
+            inputs.append((torch.tensor(rho, dtype=torch.float32, device="cuda"),
+                           torch.tensor(u, dtype=torch.float32, device="cuda")))
+
+        def reset():
+            for s, (r, uu) in zip(sims, inputs):
+                s.init_fields(r, uu)
+
+        cells = float(sum(np.prod(p["shape"]) for p, _, _ in jobs))
+        byts = float(sum(np.prod(p["shape"]) * (12 * p["lattice"] + 8) for p, _, _ in jobs))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # one job at a time
+        reset()
+        for s in sims:
+            s.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in sims:
+            s.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        loop_ms = e0.elapsed_time(e1)
+        for s in sims:
+            s.sync()
+        # together
+        reset()
+        batch = Batch(sims, stream=stream)
+        choice = batch.tune(trial_steps=2)
+        batch.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        batch_ms = e0.elapsed_time(e1)
+        batch.sync()
+        info = batch.info()
+        batch.close()
+        for s in sims:
+            s.close()
+    torch.cuda.synchronize()
+    return {"workload": BATCH_WORKLOAD, "jobs": n_jobs, "cells": int(cells), "steps": steps,
+            "gpu_bytes": int(sum(np.prod(p["shape"]) * (4 * p["lattice"] + 4) for p, _, _ in jobs)),
+            "one_at_a_time": {"mlups": cells * steps / (loop_ms * 1e-3) / 1e6, "ms": loop_ms},
+            "batched": {"mlups": cells * steps / (batch_ms * 1e-3) / 1e6, "ms": batch_ms,
+                        "hbm_frac": byts * steps / (batch_ms * 1e-3) / 1e9 / measured_peaks()[0],
+                        "groups": info["groups"], "tiles": info["tiles"], "graph_mode": info["graph_mode"],
+                        "zchunk": choice, "launches_per_step": 2 * info["groups"]},
+            "speedup": loop_ms / batch_ms}
+
+
 # ---------------------------------------------------------------- oracle timing on host cores
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -329,6 +417,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-q27", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
@@ -361,6 +451,7 @@ def main():
     value = whole_job_mlups(ws, n, args.steps, ms)
     r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
     e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
+    batched = None if (args.no_batched or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
     if rank != 0:
         return
     ab = algorithmic_bytes(19)
@@ -398,6 +489,8 @@ def main():
                          "collide_gbs": ab27["collide"] * n / (c27 * 1e-3) / 1e9, "mass_drift_rel": r27["mass_drift"]}
     if e2e:
         line["e2e"] = e2e
+    if batched:
+        line["batched"] = batched
     if ws == 1 and not args.no_cpu_baseline:
         try:
             cb = oracle_timing(19, args.cpu_seconds)

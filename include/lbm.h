@@ -172,6 +172,41 @@ size_t lbm_device_bytes(const lbm_ctx* ctx);
 /* Frees the device state.  Waits for the stream first.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent domains advanced together (the paper's method applied to a set
+ * of jobs; the paper itself runs one domain at a time).  Members are grouped by
+ * (lattice, walls or solids present, multiphase); each time step costs one
+ * collide-stream launch and one density/psi launch per group, whose blocks are
+ * tiles of every member of the group.  Per cell the arithmetic is the
+ * single-domain kernels', so every member evolves bitwise as if stepped alone.
+ * Runs of steps are replayed from one CUDA graph (a device-side loop), so n steps
+ * cost one graph launch.
+ *
+ * lbm_batch_create: ctxs are n >= 1 distinct, initialised contexts on the current
+ *   device that have taken the same number of steps modulo 2; the batch keeps the
+ *   pointers (the caller keeps ownership and must not destroy a member while the
+ *   batch exists, nor re-initialise a member with a different solid set-up).  Work
+ *   is enqueued on cuda_stream; the caller orders it with the members' streams.
+ *   Errors: LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA (message in
+ *   lbm_last_error(NULL)).
+ * lbm_batch_step: enqueues n >= 0 steps of every member (does not wait) and
+ *   advances their step counters.  LBM_ERR_STATE if members were stepped apart.
+ * lbm_batch_sync: waits and returns the first sticky member error (lbm_sync).
+ * lbm_batch_tune: times the collide launches of every group for trial_steps steps
+ *   with each candidate z-chunk (automatic, 1, 2, 4, 8, 16, 32 planes per block),
+ *   keeps the fastest per group and writes it to zchunk_out[g] for g < max_groups
+ *   (0 = automatic).  The members advance by 7 x (trial_steps + 1) steps.
+ * lbm_batch_info: number of groups, tiles of the collide launches, graph mode
+ *   (0 not recorded yet, 1 device-side WHILE loop, 2 replayed two-step graph). */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* batch, int32_t n);
+lbm_status lbm_batch_sync(lbm_batch* batch);
+lbm_status lbm_batch_tune(lbm_batch* batch, int32_t trial_steps, int32_t* zchunk_out, int32_t max_groups);
+lbm_status lbm_batch_info(const lbm_batch* batch, int32_t* ngroups, int32_t* ntiles, int32_t* graph_mode);
+void lbm_batch_destroy(lbm_batch* batch);
+const char* lbm_batch_last_error(const lbm_batch* batch);
+
 /* Totals without allocation.  The paper has no counterpart: this is a service
  * for callers that must not allocate device memory while they run (code being
  * recorded into a CUDA graph, hosts whose device memory is pre-budgeted by their

@@ -1,0 +1,419 @@
+// Multi-domain batch (lbm_batch_*): many independent domains advanced together.
+//
+// Members are grouped by (lattice, walls/solids present, multiphase).  Per time step each group
+// costs one collide-stream launch and one density/psi launch whose blocks are tiles of every
+// member of the group (a block reads its domain's parameters from a device table), instead of two
+// launches per domain.  The per-cell arithmetic is the single-domain code, so a member's result is
+// bitwise the same as stepping it alone.  Whole runs are replayed from a CUDA graph: a WHILE
+// conditional node repeats a two-step body until a device-side counter runs out, so n steps are
+// one graph launch; where conditional nodes are unavailable the two-step graph is launched n/2
+// times.  lbm_batch_tune times the candidate z-chunks per group on the live state.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "ctx_internal.h"
+#include "lbm_internal.h"
+
+using lbm::BatchTile;
+using lbm::KParams;
+
+namespace {
+
+constexpr int PSI_TILE_H = 4;   // rows of the density/psi tiles (its blocks are 32 x 4 threads)
+
+struct Group {
+    int Q = 19, solids = 0, multiphase = 0;
+    std::vector<int> members;
+    int zchunk = 0;                 // 0 = automatic
+    BatchTile* tiles = nullptr;     // collide tiles (device)
+    int ntiles = 0;
+    BatchTile* ptiles = nullptr;    // density/psi tiles (device)
+    int nptiles = 0;
+};
+
+__global__ void set_counter_kernel(int* counter, int value) { *counter = value; }
+
+// Last node of the loop body: one more two-step iteration done; stop when the count runs out.
+__global__ void loop_tick_kernel(cudaGraphConditionalHandle h, int* counter) {
+    if (--(*counter) <= 0) cudaGraphSetConditional(h, 0);
+}
+
+bool has_solid_work(const lbm_ctx* c) { return c->nbmask != nullptr || c->kp.wall_x || c->kp.wall_y || c->kp.wall_z; }
+
+}  // namespace
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> members;
+    std::vector<KParams> table;     // host copy of the member parameter table
+    std::vector<Group> groups;
+    cudaStream_t stream = nullptr;
+    KParams* doms = nullptr;        // member parameter table (device)
+    int* counter = nullptr;         // loop counter of the graph (device)
+    cudaStream_t cap = nullptr;     // capture stream
+    cudaGraphExec_t exec = nullptr;
+    int graph_parity = -1;          // AA phase the graph was recorded for
+    int graph_mode = 0;             // 0 none yet, 1 WHILE conditional node, 2 replayed two-step graph
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
+    if (b) b->err = m;
+    else lbm::set_thread_error(m.c_str());
+    return s;
+}
+
+#define BCK(b, call)                                                                                 \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,            \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+void free_tiles(Group& g) {
+    if (g.tiles) cudaFree(g.tiles);
+    if (g.ptiles) cudaFree(g.ptiles);
+    g.tiles = g.ptiles = nullptr;
+    g.ntiles = g.nptiles = 0;
+}
+
+void drop_graph(lbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_parity = -1;
+    b->graph_mode = 0;
+}
+
+// Tiles of every member of a group: 32 x h cells per tile in (x, y), z-chunks chosen so that the
+// whole group gives a few waves of resident blocks (or the group's fixed zchunk).
+lbm_status build_tiles(lbm_batch* b, Group& g) {
+    free_tiles(g);
+    const int th = g.Q == 19 ? lbm::tile_height_q19() : lbm::tile_height_q27();
+    const int resident = g.Q == 19 ? lbm::resident_blocks_q19() : lbm::resident_blocks_q27();
+    long long cols = 0;
+    for (int d : g.members) {
+        const KParams& k = b->members[d]->kp;
+        cols += (long long)((k.nx + 31) / 32) * ((k.ny + th - 1) / th);
+    }
+    const long long target = 152LL * resident * 4;
+    const long long chunks_auto = std::max(1LL, (target + cols - 1) / std::max(cols, 1LL));
+    std::vector<BatchTile> t, pt;
+    for (int d : g.members) {
+        const KParams& k = b->members[d]->kp;
+        int zc;
+        if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);
+        else {
+            const long long ch = std::min<long long>(chunks_auto, k.nz);
+            zc = (int)((k.nz + ch - 1) / ch);
+        }
+        for (int z0 = 0; z0 < k.nz; z0 += zc) {
+            for (int y0 = 0; y0 < k.ny; y0 += th)
+                for (int x0 = 0; x0 < k.nx; x0 += 32) t.push_back({d, x0, y0, z0, zc});
+            for (int y0 = 0; y0 < k.ny; y0 += PSI_TILE_H)
+                for (int x0 = 0; x0 < k.nx; x0 += 32) pt.push_back({d, x0, y0, z0, zc});
+        }
+    }
+    if (t.size() > 0x7fffffff || pt.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
+    BCK(b, cudaMalloc((void**)&g.tiles, t.size() * sizeof(BatchTile)));
+    BCK(b, cudaMalloc((void**)&g.ptiles, pt.size() * sizeof(BatchTile)));
+    BCK(b, cudaMemcpyAsync(g.tiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(g.ptiles, pt.data(), pt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    g.ntiles = (int)t.size();
+    g.nptiles = (int)pt.size();
+    return LBM_OK;
+}
+
+// One collide launch of group g at AA phase `parity` (optionally bracketed by events).
+cudaError_t collide_group(lbm_batch* b, const Group& g, int parity, cudaStream_t st) {
+    return g.Q == 19
+               ? lbm::launch_collide_batch_q19(b->doms, g.tiles, g.ntiles, parity, g.solids, g.multiphase, st)
+               : lbm::launch_collide_batch_q27(b->doms, g.tiles, g.ntiles, parity, g.solids, g.multiphase, st);
+}
+
+cudaError_t psi_group(lbm_batch* b, const Group& g, int parity, cudaStream_t st) {
+    if (!g.multiphase) return cudaSuccess;
+    return g.Q == 19 ? lbm::launch_psi_batch_q19(b->doms, g.ptiles, g.nptiles, parity, g.solids, st)
+                     : lbm::launch_psi_batch_q27(b->doms, g.ptiles, g.nptiles, parity, g.solids, st);
+}
+
+// One step of every member, starting at AA phase `parity` (psi of the current state valid).
+cudaError_t step_once(lbm_batch* b, int parity, cudaStream_t st) {
+    for (const Group& g : b->groups) {
+        cudaError_t e = collide_group(b, g, parity, st);
+        if (e != cudaSuccess) return e;
+    }
+    for (const Group& g : b->groups) {
+        cudaError_t e = psi_group(b, g, parity ^ 1, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+lbm_status record_graph(lbm_batch* b, int parity) {
+    drop_graph(b);
+    if (!b->cap) BCK(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    // first choice: one WHILE node whose body is two steps and a counter tick
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+    }
+    if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            cudaError_t e1 = step_once(b, parity, b->cap);
+            cudaError_t e2 = e1 == cudaSuccess ? step_once(b, parity ^ 1, b->cap) : e1;
+            if (e2 == cudaSuccess) {
+                loop_tick_kernel<<<1, 1, 0, b->cap>>>(h, b->counter);
+                e2 = cudaGetLastError();
+            }
+            cudaGraph_t out = nullptr;
+            cudaError_t e3 = cudaStreamEndCapture(b->cap, &out);
+            ok = e2 == cudaSuccess && e3 == cudaSuccess;
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (ok) {
+        b->graph_mode = 1;
+        b->graph_parity = parity;
+        return LBM_OK;
+    }
+    (void)cudaGetLastError();
+    b->exec = nullptr;
+    // fallback: a plain two-step graph, replayed
+    BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = step_once(b, parity, b->cap);
+    cudaError_t e2 = e1 == cudaSuccess ? step_once(b, parity ^ 1, b->cap) : e1;
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(b->cap, &g2);
+    if (e2 != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
+    if (e3 != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e3));
+    cudaError_t e4 = cudaGraphInstantiate(&b->exec, g2, 0);
+    cudaGraphDestroy(g2);
+    if (e4 != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e4));
+    b->graph_mode = 2;
+    b->graph_parity = parity;
+    return LBM_OK;
+}
+
+void advance_members(lbm_batch* b, int n) {
+    for (lbm_ctx* c : b->members) {
+        c->t += n;
+        c->parity ^= (n & 1);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return bfail(nullptr, LBM_ERR_ARG, "a batch needs at least one context");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return bfail(nullptr, LBM_ERR_ARG, "NULL context in the batch");
+        if (!ctxs[i]->initialised) return bfail(nullptr, LBM_ERR_STATE, "every context must be initialised");
+        if (ctxs[i]->parity != ctxs[0]->parity)
+            return bfail(nullptr, LBM_ERR_STATE, "all contexts must have taken an equal number of steps mod 2");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return bfail(nullptr, LBM_ERR_ARG, "a context appears twice in the batch");
+    }
+    lbm_batch* b = new lbm_batch();
+    b->members.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < n; ++i) {
+        const lbm_ctx* c = ctxs[i];
+        const int solids = has_solid_work(c) ? 1 : 0, mp = c->kp.multiphase ? 1 : 0;
+        auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const Group& g) {
+            return g.Q == c->Q && g.solids == solids && g.multiphase == mp;
+        });
+        if (it == b->groups.end()) {
+            Group g;
+            g.Q = c->Q;
+            g.solids = solids;
+            g.multiphase = mp;
+            b->groups.push_back(g);
+            it = b->groups.end() - 1;
+        }
+        it->members.push_back(i);
+    }
+    b->table.resize(n);
+    for (int i = 0; i < n; ++i) b->table[i] = ctxs[i]->kp;
+    lbm_status s = LBM_OK;
+    cudaError_t e = cudaMalloc((void**)&b->doms, n * sizeof(KParams));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->counter, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->doms, b->table.data(), n * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) s = bfail(nullptr, LBM_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    for (size_t k = 0; s == LBM_OK && k < b->groups.size(); ++k) {
+        s = build_tiles(b, b->groups[k]);
+        if (s != LBM_OK) lbm::set_thread_error(b->err.c_str());
+    }
+    if (s != LBM_OK) {
+        lbm_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int32_t n) {
+    if (!b) return LBM_ERR_ARG;
+    if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
+    const int parity = b->members[0]->parity;
+    bool changed = false;
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        const lbm_ctx* c = b->members[i];
+        if (c->parity != parity) return bfail(b, LBM_ERR_STATE, "members were stepped apart: AA phases differ");
+        if (c->sticky != LBM_OK) return bfail(b, c->sticky, "a member has a sticky error: " + c->err);
+        if (memcmp(&b->table[i], &c->kp, sizeof(KParams)) != 0) {
+            b->table[i] = c->kp;
+            changed = true;
+        }
+    }
+    if (changed)   // a member was re-initialised (e.g. its solid mask moved): refresh the device table
+        BCK(b, cudaMemcpyAsync(b->doms, b->table.data(), b->table.size() * sizeof(KParams), cudaMemcpyHostToDevice,
+                               b->stream));
+    int done = 0;
+    if (n >= 2) {
+        if (b->graph_parity != parity) {
+            lbm_status s = record_graph(b, parity);
+            if (s != LBM_OK) return s;
+        }
+        const int pairs = n / 2;
+        if (b->graph_mode == 1) {
+            set_counter_kernel<<<1, 1, 0, b->stream>>>(b->counter, pairs);
+            BCK(b, cudaGetLastError());
+            BCK(b, cudaGraphLaunch(b->exec, b->stream));
+        } else {
+            for (int k = 0; k < pairs; ++k) BCK(b, cudaGraphLaunch(b->exec, b->stream));
+        }
+        done = 2 * pairs;
+    }
+    if (done < n) BCK(b, step_once(b, parity, b->stream));
+    advance_members(b, n);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    if (!b) return LBM_ERR_ARG;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    lbm_status first = LBM_OK;
+    for (lbm_ctx* c : b->members) {
+        lbm_status s = lbm_sync(c);
+        if (s != LBM_OK && first == LBM_OK) {
+            first = s;
+            b->err = lbm_last_error(c);
+        }
+    }
+    return first;
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out, int32_t max_groups) {
+    if (!b) return LBM_ERR_ARG;
+    if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "trial_steps must be >= 1");
+    const int cand[] = {0, 1, 2, 4, 8, 16, 32};
+    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+    const size_t G = b->groups.size();
+    std::vector<double> best(G, 1e300);
+    std::vector<int> choice(G, 0);
+    std::vector<cudaEvent_t> ev(2 * G * trial_steps);
+    for (auto& e : ev) BCK(b, cudaEventCreate(&e));
+    lbm_status result = LBM_OK;
+    for (int ci = 0; ci < nc && result == LBM_OK; ++ci) {
+        for (Group& g : b->groups) {
+            g.zchunk = cand[ci];
+            result = build_tiles(b, g);
+            if (result != LBM_OK) break;
+        }
+        if (result != LBM_OK) break;
+        drop_graph(b);
+        int parity = b->members[0]->parity;
+        // one untimed step, then per-group events around every collide launch
+        cudaError_t e = step_once(b, parity, b->stream);
+        parity ^= 1;
+        for (int s = 0; s < trial_steps && e == cudaSuccess; ++s) {
+            for (size_t k = 0; k < G && e == cudaSuccess; ++k) {
+                e = cudaEventRecord(ev[2 * (s * G + k)], b->stream);
+                if (e == cudaSuccess) e = collide_group(b, b->groups[k], parity, b->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (s * G + k) + 1], b->stream);
+            }
+            for (size_t k = 0; k < G && e == cudaSuccess; ++k) e = psi_group(b, b->groups[k], parity ^ 1, b->stream);
+            parity ^= 1;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            result = bfail(b, LBM_ERR_CUDA, std::string("tuning: ") + cudaGetErrorString(e));
+            break;
+        }
+        advance_members(b, trial_steps + 1);
+        for (size_t k = 0; k < G; ++k) {
+            double tot = 0.0;
+            for (int s = 0; s < trial_steps; ++s) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * (s * G + k)], ev[2 * (s * G + k) + 1]);
+                tot += ms;
+            }
+            if (tot < best[k]) {
+                best[k] = tot;
+                choice[k] = cand[ci];
+            }
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (result != LBM_OK) return result;
+    for (size_t k = 0; k < G; ++k) {
+        b->groups[k].zchunk = choice[k];
+        lbm_status s = build_tiles(b, b->groups[k]);
+        if (s != LBM_OK) return s;
+        if (zchunk_out && (int)k < max_groups) zchunk_out[k] = choice[k];
+    }
+    drop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch* b, int32_t* ngroups, int32_t* ntiles, int32_t* graph_mode) {
+    if (!b) return LBM_ERR_ARG;
+    if (ngroups) *ngroups = (int32_t)b->groups.size();
+    if (ntiles) {
+        long long t = 0;
+        for (const Group& g : b->groups) t += g.ntiles;
+        *ntiles = (int32_t)std::min<long long>(t, 0x7fffffff);
+    }
+    if (graph_mode) *graph_mode = b->graph_mode;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    if (b->stream || b->doms) (void)cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (Group& g : b->groups) free_tiles(g);
+    if (b->doms) cudaFree(b->doms);
+    if (b->counter) cudaFree(b->counter);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : lbm_last_error(nullptr); }
+
+}  // extern "C"

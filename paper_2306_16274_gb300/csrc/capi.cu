@@ -9,39 +9,9 @@
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
+#include "ctx_internal.h"
 
 using lbm::KParams;
-
-struct lbm_ctx {
-    lbm_params p{};
-    int Q = 19;
-    KParams kp{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    // device state
-    float* f = nullptr;          // Q planes of `plane` floats (AA layout)
-    float* psi = nullptr;        // ncell floats
-    uint32_t* nbmask = nullptr;  // ncell words, only when a solid mask was given
-    unsigned* status = nullptr;  // device status word
-    double* partials = nullptr;  // moments partial sums (4 per block)
-    double* sums = nullptr;      // 4 doubles
-    float* staging = nullptr;    // ncell * max(Q, 4) floats for host transfers
-    uint8_t* solid_dev = nullptr;
-    size_t bytes = 0;
-    long long partial_blocks = 0;
-    // host state
-    int parity = 0;              // 0: natural layout, 1: swapped (after an odd number of AA steps)
-    long long t = 0;
-    bool initialised = false;
-    lbm_status sticky = LBM_OK;
-    std::string err;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;
-    size_t ev_used = 0;
-    double ms[2] = {0.0, 0.0};
-    long long launches[2] = {0, 0};
-};
 
 namespace {
 
@@ -272,6 +242,8 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         for (int i = 0; i < c->Q; ++i) c->kp.fq[i] = c->f + (size_t)i * plane;
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
+    c->kp.psi = c->psi;
+    c->kp.status = c->status;
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
     if (e == cudaSuccess) e = alloc((void**)&c->sums, 4 * sizeof(double));
     if (e == cudaSuccess) e = alloc((void**)&c->staging, (size_t)stage_w * n * sizeof(float));
@@ -318,6 +290,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->bytes -= n * sizeof(uint32_t);
         c->nbmask = nullptr;
     }
+    c->kp.nbmask = c->nbmask;
     CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream)
                      : lbm::launch_init_q27(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream));
     c->parity = 0;

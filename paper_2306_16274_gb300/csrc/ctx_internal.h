@@ -1,0 +1,41 @@
+// Internal layout of an lbm_ctx, shared by the C ABI (capi.cu) and the multi-domain batch
+// (batch.cu).  Not part of the public interface.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+struct lbm_ctx {
+    lbm_params p{};
+    int Q = 19;
+    lbm::KParams kp{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // device state
+    float* f = nullptr;          // Q planes of `plane` floats (AA layout)
+    float* psi = nullptr;        // ncell floats
+    uint32_t* nbmask = nullptr;  // ncell words, only when a solid mask was given
+    unsigned* status = nullptr;  // device status word
+    double* partials = nullptr;  // moments partial sums (4 per block)
+    double* sums = nullptr;      // 4 doubles
+    float* staging = nullptr;    // ncell * max(Q, 4) floats for host transfers
+    uint8_t* solid_dev = nullptr;
+    size_t bytes = 0;
+    long long partial_blocks = 0;
+    // host state
+    int parity = 0;              // 0: natural layout, 1: swapped (after an odd number of AA steps)
+    long long t = 0;
+    bool initialised = false;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double ms[2] = {0.0, 0.0};
+    long long launches[2] = {0, 0};
+};
+

@@ -15,27 +15,55 @@ constexpr int Q = LBM_Q;
 // ---- density + psi pass (Sec. II A, Sec. II C): one thread per cell, x fastest
 constexpr int PSI_BX = 32, PSI_BY = 4;
 
+// cells (x, y, z) for z in [z0, z1) of one column
+template <int PARITY, bool SOLIDS>
+__device__ __forceinline__ void psi_column(const KParams& kp, const float* __restrict__ f, float* __restrict__ psi,
+                                           const uint32_t* __restrict__ nbmask, unsigned* status, int x, int y,
+                                           int z0, int z1) {
+    if (x >= kp.nx || y >= kp.ny) return;
+    for (int z = z0; z < z1; ++z) {
+        const Cell c = make_cell(kp, x, y, z);
+        const uint32_t bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+        if (bits & 1u) {
+            psi[c.idx] = 0.0f;
+            continue;
+        }
+        float p[Q];
+        gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+        float rho = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += p[i];
+        psi[c.idx] = eval_psi(kp, rho, status);
+    }
+}
+
 template <int PARITY, bool SOLIDS>
 __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const float* __restrict__ f,
                                                             float* __restrict__ psi,
                                                             const uint32_t* __restrict__ nbmask,
                                                             unsigned* status) {
-    const int x = blockIdx.x * PSI_BX + threadIdx.x;
-    const int y = blockIdx.y * PSI_BY + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= kp.nx || y >= kp.ny) return;
-    const Cell c = make_cell(kp, x, y, z);
-    const uint32_t bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
-    if (bits & 1u) {
-        psi[c.idx] = 0.0f;
-        return;
-    }
-    float p[Q];
-    gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
-    float rho = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) rho += p[i];
-    psi[c.idx] = eval_psi(kp, rho, status);
+    psi_column<PARITY, SOLIDS>(kp, f, psi, nbmask, status, blockIdx.x * PSI_BX + threadIdx.x,
+                               blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1);
+}
+
+// The block's domain parameters, copied from the domain table into shared memory (read uniformly).
+__device__ __forceinline__ void load_domain(KParams& dst, const KParams* __restrict__ doms, int d) {
+    const unsigned* src = reinterpret_cast<const unsigned*>(doms + d);
+    unsigned* out = reinterpret_cast<unsigned*>(&dst);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    for (int k = tid; k < (int)(sizeof(KParams) / sizeof(unsigned)); k += blockDim.x * blockDim.y) out[k] = src[k];
+}
+
+// multi-domain density + psi pass: one block per tile of any domain
+template <int PARITY, bool SOLIDS>
+__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParams* __restrict__ doms,
+                                                                  const BatchTile* __restrict__ tiles) {
+    __shared__ KParams skp;
+    const BatchTile t = tiles[blockIdx.x];
+    load_domain(skp, doms, t.d);
+    __syncthreads();
+    psi_column<PARITY, SOLIDS>(skp, skp.fq[0], skp.psi, skp.nbmask, skp.status, t.x0 + threadIdx.x,
+                               t.y0 + threadIdx.y, t.z0, min(t.z0 + t.zc, skp.nz));
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
@@ -89,13 +117,12 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 #define LBM_ZM_PREFETCH 1
 #endif
 
+// One tile: cells [x0, x0+32) x [y0, y0+ZM_BY) marching through planes [z0, z0+zchunk).
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
-                                                                const uint32_t* __restrict__ nbmask,
-                                                                unsigned* status, int zchunk) {
-    __shared__ float ring[4][ZM_RP];
+__device__ __forceinline__ void collide_tile(const KParams& kp, const float* __restrict__ psi,
+                                             const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
+                                             int z0, int zchunk, float (*ring)[ZM_RP]) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
-    const int x0 = blockIdx.x * ZM_BX, y0 = blockIdx.y * ZM_BY, z0 = blockIdx.z * zchunk;
     const int x = x0 + tx, y = y0 + ty;
     const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
     const bool act_xy = x < nx && y < ny;
@@ -178,6 +205,27 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
         if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
         store32<Q, PARITY, SOLIDS>(kp, o, bits, p);
     }
+}
+
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
+                                                                const uint32_t* __restrict__ nbmask,
+                                                                unsigned* status, int zchunk) {
+    __shared__ float ring[4][ZM_RP];
+    collide_tile<PARITY, SOLIDS, MULTIPHASE>(kp, psi, nbmask, status, blockIdx.x * ZM_BX, blockIdx.y * ZM_BY,
+                                             blockIdx.z * zchunk, zchunk, ring);
+}
+
+// multi-domain collide-stream pass: one block per tile of any domain
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KParams* __restrict__ doms,
+                                                                      const BatchTile* __restrict__ tiles) {
+    __shared__ float ring[4][ZM_RP];
+    __shared__ KParams skp;
+    const BatchTile t = tiles[blockIdx.x];
+    load_domain(skp, doms, t.d);
+    __syncthreads();
+    collide_tile<PARITY, SOLIDS, MULTIPHASE>(skp, skp.psi, skp.nbmask, skp.status, t.x0, t.y0, t.z0, t.zc, ring);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -407,6 +455,38 @@ cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int 
         default: return launch_collide_variant<1, true, true>(g, b, st, kp, psi, nbmask, status, zc);
     }
 }
+
+cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams* doms, const BatchTile* tiles, int ntiles,
+                                                   int parity, int solids, int multiphase, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    const dim3 b(ZM_BX, ZM_BY);
+    const int key = parity * 4 + (solids ? 2 : 0) + (multiphase ? 1 : 0);
+    switch (key) {
+        case 0: collide_batch_kernel<0, false, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 1: collide_batch_kernel<0, false, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 2: collide_batch_kernel<0, true, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 3: collide_batch_kernel<0, true, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 4: collide_batch_kernel<1, false, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 5: collide_batch_kernel<1, false, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 6: collide_batch_kernel<1, true, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        default: collide_batch_kernel<1, true, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams* doms, const BatchTile* tiles, int ntiles, int parity,
+                                               int solids, cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    const dim3 b(PSI_BX, PSI_BY);
+    if (parity == 0 && !solids) psi_batch_kernel<0, false><<<ntiles, b, 0, st>>>(doms, tiles);
+    else if (parity == 0) psi_batch_kernel<0, true><<<ntiles, b, 0, st>>>(doms, tiles);
+    else if (!solids) psi_batch_kernel<1, false><<<ntiles, b, 0, st>>>(doms, tiles);
+    else psi_batch_kernel<1, true><<<ntiles, b, 0, st>>>(doms, tiles);
+    return cudaGetLastError();
+}
+
+int LBM_CAT(tile_height_q, LBM_Q)() { return ZM_BY; }
+int LBM_CAT(resident_blocks_q, LBM_Q)() { return ZM_MINB; }
 
 cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, float* f, const float* rho, const float* u,
                                           const uint32_t* nbmask, cudaStream_t st) {

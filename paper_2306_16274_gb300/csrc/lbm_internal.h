@@ -40,6 +40,16 @@ struct KParams {
     float gx, gy, gz;             // body force per unit mass
     float* fq[27];                // base of population plane i (f + i * plane); cells < 2^31
     int zchunk;                   // z planes per collide block (0 = automatic)
+    // device buffers of the domain (used by the multi-domain kernels, which read KParams from memory)
+    float* psi;
+    const uint32_t* nbmask;
+    unsigned* status;
+};
+
+// One block of a multi-domain launch: domain d, cells [x0, x0+32) x [y0, y0+tile height)
+// x [z0, z0+zc) (clipped to the domain).
+struct BatchTile {
+    int d, x0, y0, z0, zc;
 };
 
 // Launchers (one set per lattice).  parity: 0 = natural layout (even AA step),
@@ -56,7 +66,13 @@ struct KParams {
                                     const float* psi, const uint32_t* nbmask, float* rho, float* u,  \
                                     double* partials, int* nblocks, cudaStream_t st);               \
     cudaError_t launch_gather_q##Q(const KParams& kp, int parity, int solids, const float* f,       \
-                                   const uint32_t* nbmask, float* out, cudaStream_t st);
+                                   const uint32_t* nbmask, float* out, cudaStream_t st);              \
+    cudaError_t launch_collide_batch_q##Q(const KParams* doms, const BatchTile* tiles, int ntiles,   \
+                                          int parity, int solids, int multiphase, cudaStream_t st);  \
+    cudaError_t launch_psi_batch_q##Q(const KParams* doms, const BatchTile* tiles, int ntiles,       \
+                                      int parity, int solids, cudaStream_t st);                      \
+    int tile_height_q##Q();                                                                         \
+    int resident_blocks_q##Q();
 
 LBM_DECLARE_LAUNCHERS(19)
 LBM_DECLARE_LAUNCHERS(27)

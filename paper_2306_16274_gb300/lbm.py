@@ -72,6 +72,13 @@ def lib():
         "lbm_last_error": (ctypes.c_char_p, [P]),
         "lbm_status_string": (ctypes.c_char_p, [I32]),
         "lbm_field_totals_noalloc": (I32, [P, P, I64, P, P]),
+        "lbm_batch_create": (I32, [ctypes.POINTER(P), I32, P, ctypes.POINTER(P)]),
+        "lbm_batch_step": (I32, [P, I32]),
+        "lbm_batch_sync": (I32, [P]),
+        "lbm_batch_tune": (I32, [P, I32, ctypes.POINTER(I32), I32]),
+        "lbm_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "lbm_batch_destroy": (V, [P]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -303,6 +310,64 @@ class Simulation:
         if getattr(self, "_ctx", None):
             self._L.lbm_destroy(self._ctx)
             self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many Simulations advanced together (lbm_batch_*): one launch per kernel and group per step,
+    runs of steps replayed from one CUDA graph.  The Simulations stay owned by the caller and must
+    outlive the Batch."""
+
+    def __init__(self, sims, stream=None):
+        self._L = lib()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s._ctx.value for s in self.sims])
+        out = ctypes.c_void_p()
+        self.stream = _stream_handle(stream)
+        st = self._L.lbm_batch_create(arr, len(self.sims), ctypes.c_void_p(self.stream), ctypes.byref(out))
+        if st != 0:
+            raise LBMError(st, self._L.lbm_last_error(None).decode())
+        self._b = out
+
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._L.lbm_batch_last_error(self._b).decode())
+
+    def step(self, n=1):
+        self._check(self._L.lbm_batch_step(self._b, int(n)))
+        return self
+
+    def sync(self):
+        self._check(self._L.lbm_batch_sync(self._b))
+
+    def tune(self, trial_steps=3):
+        """Pick the z-chunk per group by timing; returns the choices (0 = automatic)."""
+        g = ctypes.c_int32()
+        self._check(self._L.lbm_batch_info(self._b, ctypes.byref(g), None, None))
+        out = (ctypes.c_int32 * max(g.value, 1))()
+        self._check(self._L.lbm_batch_tune(self._b, int(trial_steps), out, g.value))
+        return list(out)[:g.value]
+
+    def info(self):
+        g, t, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._L.lbm_batch_info(self._b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(m)))
+        return {"groups": g.value, "tiles": t.value, "graph_mode": m.value}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.lbm_batch_destroy(self._b)
+            self._b = None
 
     def __enter__(self):
         return self

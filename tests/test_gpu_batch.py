@@ -1,0 +1,121 @@
+"""Multi-domain batches (lbm_batch_*): every member must evolve bitwise as when stepped alone,
+whatever the grouping, tiling, graph replay or tuning."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _members():
+    """(params dict, rho, u, solid) for a mixed set: both lattices, periodic droplets, a walled
+    impact with interior solids, a single-phase domain, ragged sizes."""
+    kw7, rl7, rv7 = U.cs_eos("T0.7")
+    kwp, rlp, rvp = U.pw_eos()
+    out = []
+    shape = (37, 21, 18)
+    out.append((dict(lattice=19, shape=shape, sigma=0.1, kappa=0.3, **kw7), *W.droplet(shape, 6.0, rl7, rv7), None))
+    shape = (33, 30, 26)
+    out.append((dict(lattice=27, shape=shape, sigma=0.1, **kw7), *W.droplet(shape, 7.0, rl7, rv7), None))
+    shape = (40, 18, 22)
+    rho, u = W.impact(shape, 6.0, rlp, rvp, U=0.03, gap=3.0)
+    solid = W.cylinder_mask(shape, 3.0, axis="y")
+    out.append((dict(lattice=19, shape=shape, bc=(0, 0, 1), sigma=0.1, G_ads=0.1, **kwp), rho, u, solid))
+    shape = (24, 24, 30)
+    rho, u = W.impact(shape, 5.0, rl7, rv7, U=0.02, gap=3.0)
+    out.append((dict(lattice=27, shape=shape, bc=(0, 0, 1), sigma=0.1, G_ads=-0.05, **kw7), rho, u, None))
+    shape = (29, 11, 13)
+    out.append((dict(lattice=19, shape=shape, g=(1e-5, 0.0, 0.0)), *W.perturbed(shape, seed=4), None))
+    shape = (48, 40, 36)
+    out.append((dict(lattice=19, shape=shape, sigma=0.1, kappa=0.5, **kw7), *W.droplet(shape, 9.0, rl7, rv7), None))
+    return out
+
+
+def _make(members):
+    return [U.run_gpu(d, rho, u, solid) for (d, rho, u, solid) in members]
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 7, 40])
+def test_batch_equals_members_stepped_alone(nsteps):
+    from paper_2306_16274_gb300 import Batch
+    m = _members()
+    alone = _make(m)
+    together = _make(m)
+    for s in alone:
+        s.step(nsteps)
+    b = Batch(together)
+    b.step(nsteps)
+    b.sync()
+    info = b.info()
+    assert info["groups"] == 5
+    if nsteps >= 2:
+        assert info["graph_mode"] in (1, 2)
+    for a, t in zip(alone, together):
+        assert t.step_count == a.step_count == nsteps
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
+        ra, ua, _ = a.moments()
+        rt, ut, _ = t.moments()
+        assert np.array_equal(ra.cpu().numpy(), rt.cpu().numpy())
+    b.close()
+
+
+def test_batch_replay_and_tuning_keep_results():
+    # several graph launches (recorded once), a tuning pass that re-tiles every group, more steps
+    from paper_2306_16274_gb300 import Batch
+    m = _members()
+    alone = _make(m)
+    together = _make(m)
+    b = Batch(together)
+    b.step(6)
+    b.step(5)
+    choice = b.tune(trial_steps=2)
+    assert len(choice) == b.info()["groups"]
+    b.step(8)
+    b.sync()
+    total = together[0].step_count
+    assert total == 6 + 5 + 7 * 3 + 8
+    for a in alone:
+        a.step(total)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
+    b.close()
+
+
+def test_batch_member_against_oracle():
+    from paper_2306_16274_gb300 import Batch
+    (d, rho, u, solid) = _members()[2]          # walled impact with a cylinder, piecewise EOS
+    sim = U.run_gpu(d, rho, u, solid)
+    b = Batch([sim])
+    b.step(60)
+    b.sync()
+    ref = U.run_oracle(d, rho, u, solid, steps=60)
+    er, eu, _, _ = U.compare_moments(sim, ref)
+    assert er < 1e-4 and eu < 1e-4, (er, eu)
+    b.close()
+
+
+def test_batch_rejects_mixed_phases_and_duplicates():
+    from paper_2306_16274_gb300 import Batch, LBMError
+    m = _members()[:2]
+    sims = _make(m)
+    sims[0].step(1)
+    with pytest.raises(LBMError) as e:
+        Batch(sims)
+    assert e.value.status == 7
+    with pytest.raises(LBMError):
+        Batch([sims[1], sims[1]])
+    sims[1].step(1)
+    b = Batch(sims)
+    sims[0].step(1)                              # stepped apart after the batch was made
+    with pytest.raises(LBMError) as e:
+        b.step(2)
+    assert e.value.status == 7
+    b.close()

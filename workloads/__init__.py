@@ -44,13 +44,14 @@ def tanh_profile(r, R, rho_l, rho_v, W):
 
 def droplet(shape, R, rho_l, rho_v, W=2.0, center=None, periodic=True):
     nx, ny, nz = shape
-    x, y, z = _grid(shape)
     c = center if center is not None else (nx / 2.0, ny / 2.0, nz / 2.0)
-    d = [x - c[0], y - c[1], z - c[2]]
-    if periodic:
-        for k, n in enumerate((nx, ny, nz)):
-            d[k] = d[k] - n * np.round(d[k] / n)
-    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    d = []
+    for k, n in enumerate((nx, ny, nz)):
+        dk = np.arange(n, dtype=np.float64) - c[k]
+        if periodic:
+            dk = dk - n * np.round(dk / n)
+        d.append(dk)
+    r = np.sqrt(d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2)
     rho = tanh_profile(r, R, rho_l, rho_v, W)
     return rho, np.zeros((3,) + rho.shape)
 
