@@ -1,10 +1,13 @@
 // Multi-domain batch (lbm_batch_*): many independent domains advanced together.
 //
-// Members are grouped by (lattice, walls/solids present, multiphase).  Per time step each group
+// Members are grouped by (lattice, solid handling, physical parameters).  Per time step each group
 // costs one collide-stream launch and one density/psi launch whose blocks are tiles of every
-// member of the group (a block reads its domain's parameters from a device table), instead of two
-// launches per domain.  The per-cell arithmetic is the single-domain code, so a member's result is
-// bitwise the same as stepping it alone.  Whole runs are replayed from a CUDA graph: a WHILE
+// member of the group (up to 64 members per launch), instead of two launches per domain.  The
+// group's physical parameters (rates, equation of state, forces) and the launch's member table
+// (geometry and buffer addresses, 64 bytes a member) are passed by value in the kernel
+// parameters, so a block reads them from the constant bank as the single-domain kernel does.
+// The per-cell arithmetic is the single-domain code, so a member's result is bitwise the same
+// as stepping it alone.  Whole runs are replayed from a CUDA graph: a WHILE
 // conditional node repeats a two-step body until a device-side counter runs out, so n steps are
 // one graph launch; where conditional nodes are unavailable the two-step graph is launched n/2
 // times.  lbm_batch_tune times the candidate z-chunks per group on the live state.
@@ -17,6 +20,8 @@
 #include "ctx_internal.h"
 #include "lbm_internal.h"
 
+using lbm::BatchDom;
+using lbm::BatchDomTable;
 using lbm::BatchTile;
 using lbm::KParams;
 
@@ -24,10 +29,20 @@ namespace {
 
 constexpr int PSI_TILE_H = 4;   // rows of the density/psi tiles (its blocks are 32 x 4 threads)
 
+// One launch of a group: up to BATCH_LAUNCH_DOMS members and their tile ranges in the group's
+// tile arrays.
+struct Launch {
+    BatchDomTable tab{};
+    int t0 = 0, nt = 0;             // collide tiles
+    int p0 = 0, np = 0;             // density/psi tiles
+};
+
 struct Group {
-    int Q = 19, solids = 0, multiphase = 0;
-    std::vector<int> members;
+    int Q = 19, solids = 0;
+    KParams phys{};                 // physical parameters shared by the members (geometry zeroed)
+    std::vector<int> members;       // members with tiles in this group
     int zchunk = 0;                 // 0 = automatic
+    std::vector<Launch> launches;
     BatchTile* tiles = nullptr;     // collide tiles (device)
     int ntiles = 0;
     BatchTile* ptiles = nullptr;    // density/psi tiles (device)
@@ -43,14 +58,43 @@ __global__ void loop_tick_kernel(cudaGraphConditionalHandle h, int* counter) {
 
 bool has_solid_work(const lbm_ctx* c) { return c->nbmask != nullptr || c->kp.wall_x || c->kp.wall_y || c->kp.wall_z; }
 
+// The physical part of a member's parameters: geometry, addresses and tiling fields zeroed, so
+// that members with equal physics compare equal byte for byte.
+KParams physics_of(const KParams& k) {
+    KParams p;
+    std::memcpy(&p, &k, sizeof(KParams));
+    p.nx = p.ny = p.nz = 0;
+    p.wall_x = p.wall_y = p.wall_z = 0;
+    p.plane = p.ncell = 0;
+    for (float*& q : p.fq) q = nullptr;
+    p.zchunk = 0;
+    return p;
+}
+
+BatchDom dom_of(const lbm_ctx* c) {
+    BatchDom d{};
+    d.nx = c->kp.nx;
+    d.ny = c->kp.ny;
+    d.nz = c->kp.nz;
+    d.wall_x = c->kp.wall_x;
+    d.wall_y = c->kp.wall_y;
+    d.wall_z = c->kp.wall_z;
+    d.plane = c->kp.plane;
+    d.base = c->kp.fq[0];
+    d.psi = c->psi;
+    d.nbmask = c->nbmask;
+    d.status = c->status;
+    return d;
+}
+
 }  // namespace
 
 struct lbm_batch {
     std::vector<lbm_ctx*> members;
-    std::vector<KParams> table;     // host copy of the member parameter table
+    std::vector<KParams> seen;      // member parameters the groups were built from
+    std::vector<BatchDom> table;    // member geometry and addresses the groups were built from
     std::vector<Group> groups;
     cudaStream_t stream = nullptr;
-    KParams* doms = nullptr;        // member parameter table (device)
     int* counter = nullptr;         // loop counter of the graph (device)
     cudaStream_t cap = nullptr;     // capture stream
     cudaGraphExec_t exec = nullptr;
@@ -80,6 +124,7 @@ void free_tiles(Group& g) {
     if (g.ptiles) cudaFree(g.ptiles);
     g.tiles = g.ptiles = nullptr;
     g.ntiles = g.nptiles = 0;
+    g.launches.clear();
 }
 
 void drop_graph(lbm_batch* b) {
@@ -89,8 +134,18 @@ void drop_graph(lbm_batch* b) {
     b->graph_mode = 0;
 }
 
-// Tiles of every member of a group: 32 x h cells per tile in (x, y), z-chunks chosen so that the
-// whole group gives a few waves of resident blocks (or the group's fixed zchunk).
+// Does the x/y column range or the z plane range of a tile touch a wall?  Walls are the planes
+// just outside a wall axis, so only the first and last cells of that axis see them.
+bool tile_touches_wall(const KParams& k, int x0, int w, int y0, int h, int z0, int zc) {
+    return (k.wall_x && (x0 == 0 || x0 + w >= k.nx)) || (k.wall_y && (y0 == 0 || y0 + h >= k.ny)) ||
+           (k.wall_z && (z0 == 0 || z0 + zc >= k.nz));
+}
+
+// Tiles of the members of a group: 32 x h cells per tile in (x, y), z-chunks chosen so that the
+// whole group gives a few waves of resident blocks (or the group's fixed zchunk).  In a group
+// without solid handling, members whose only solids are domain walls contribute their interior
+// tiles; their wall-touching tiles (with single-plane chunks at z walls) go to the matching
+// solid-handling group, so only the boundary shell pays for the solid tests.
 lbm_status build_tiles(lbm_batch* b, Group& g) {
     free_tiles(g);
     const int th = g.Q == 19 ? lbm::tile_height_q19() : lbm::tile_height_q27();
@@ -103,26 +158,61 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
     const long long target = 152LL * resident * 4;
     const long long chunks_auto = std::max(1LL, (target + cols - 1) / std::max(cols, 1LL));
     std::vector<BatchTile> t, pt;
-    for (int d : g.members) {
-        const KParams& k = b->members[d]->kp;
+    for (size_t j = 0; j < g.members.size(); ++j) {
+        const int d = (int)(j % lbm::BATCH_LAUNCH_DOMS);   // slot in the launch's member table
+        if (d == 0) {
+            g.launches.emplace_back();
+            g.launches.back().t0 = (int)t.size();
+            g.launches.back().p0 = (int)pt.size();
+        }
+        Launch& L = g.launches.back();
+        L.tab.d[d] = b->table[g.members[j]];
+        const lbm_ctx* c = b->members[g.members[j]];
+        const KParams& k = c->kp;
+        const bool walls_only = c->nbmask == nullptr && (k.wall_x || k.wall_y || k.wall_z);
         int zc;
         if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);
         else {
             const long long ch = std::min<long long>(chunks_auto, k.nz);
             zc = (int)((k.nz + ch - 1) / ch);
         }
-        for (int z0 = 0; z0 < k.nz; z0 += zc) {
-            for (int y0 = 0; y0 < k.ny; y0 += th)
-                for (int x0 = 0; x0 < k.nx; x0 += 32) t.push_back({d, x0, y0, z0, zc});
-            for (int y0 = 0; y0 < k.ny; y0 += PSI_TILE_H)
-                for (int x0 = 0; x0 < k.nx; x0 += 32) pt.push_back({d, x0, y0, z0, zc});
+        // z-chunk boundaries: single planes at z walls, zc-plane chunks in between
+        std::vector<std::pair<int, int>> zr;
+        int zlo = 0, zhi = k.nz;
+        if (walls_only && k.wall_z) {
+            zr.push_back({0, 1});
+            if (k.nz > 1) zr.push_back({k.nz - 1, 1});
+            zlo = 1;
+            zhi = k.nz - 1;
         }
+        for (int z0 = zlo; z0 < zhi; z0 += zc) zr.push_back({z0, std::min(zc, zhi - z0)});
+        for (const auto& r : zr) {
+            for (int y0 = 0; y0 < k.ny; y0 += th)
+                for (int x0 = 0; x0 < k.nx; x0 += 32) {
+                    const bool wall = tile_touches_wall(k, x0, 32, y0, th, r.first, r.second);
+                    const bool mine = !walls_only || (wall == (g.solids != 0));
+                    if (mine) t.push_back({d, x0, y0, r.first, r.second});
+                }
+            for (int y0 = 0; y0 < k.ny; y0 += PSI_TILE_H)
+                for (int x0 = 0; x0 < k.nx; x0 += 32) {
+                    const bool wall = tile_touches_wall(k, x0, 32, y0, PSI_TILE_H, r.first, r.second);
+                    const bool mine = !walls_only || (wall == (g.solids != 0));
+                    if (mine) pt.push_back({d, x0, y0, r.first, r.second});
+                }
+        }
+        L.nt = (int)t.size() - L.t0;
+        L.np = (int)pt.size() - L.p0;
     }
     if (t.size() > 0x7fffffff || pt.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
-    BCK(b, cudaMalloc((void**)&g.tiles, t.size() * sizeof(BatchTile)));
-    BCK(b, cudaMalloc((void**)&g.ptiles, pt.size() * sizeof(BatchTile)));
-    BCK(b, cudaMemcpyAsync(g.tiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
-    BCK(b, cudaMemcpyAsync(g.ptiles, pt.data(), pt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    if (!t.empty()) {
+        BCK(b, cudaMalloc((void**)&g.tiles, t.size() * sizeof(BatchTile)));
+        BCK(b, cudaMemcpyAsync(g.tiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    }
+    if (!pt.empty()) {
+        BCK(b, cudaMalloc((void**)&g.ptiles, pt.size() * sizeof(BatchTile)));
+        BCK(b, cudaMemcpyAsync(g.ptiles, pt.data(), pt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
+                               b->stream));
+    }
     BCK(b, cudaStreamSynchronize(b->stream));
     g.ntiles = (int)t.size();
     g.nptiles = (int)pt.size();
@@ -130,26 +220,81 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
 }
 
 // One collide launch of group g at AA phase `parity` (optionally bracketed by events).
-cudaError_t collide_group(lbm_batch* b, const Group& g, int parity, cudaStream_t st) {
-    return g.Q == 19
-               ? lbm::launch_collide_batch_q19(b->doms, g.tiles, g.ntiles, parity, g.solids, g.multiphase, st)
-               : lbm::launch_collide_batch_q27(b->doms, g.tiles, g.ntiles, parity, g.solids, g.multiphase, st);
+cudaError_t collide_group(const Group& g, int parity, cudaStream_t st) {
+    for (const Launch& L : g.launches) {
+        const BatchTile* t = g.tiles + L.t0;
+        cudaError_t e = g.Q == 19 ? lbm::launch_collide_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, st)
+                                  : lbm::launch_collide_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-cudaError_t psi_group(lbm_batch* b, const Group& g, int parity, cudaStream_t st) {
-    if (!g.multiphase) return cudaSuccess;
-    return g.Q == 19 ? lbm::launch_psi_batch_q19(b->doms, g.ptiles, g.nptiles, parity, g.solids, st)
-                     : lbm::launch_psi_batch_q27(b->doms, g.ptiles, g.nptiles, parity, g.solids, st);
+cudaError_t psi_group(const Group& g, int parity, cudaStream_t st) {
+    if (!g.phys.multiphase) return cudaSuccess;
+    for (const Launch& L : g.launches) {
+        const BatchTile* t = g.ptiles + L.p0;
+        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.np, parity, g.solids, st)
+                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.np, parity, g.solids, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// (Re)build the groups, their member tables and tiles from the members' current parameters.  Walls-only members join both the plain group (interior tiles) and the
+// solid-handling group (boundary tiles) of their physics.
+lbm_status regroup(lbm_batch* b) {
+    drop_graph(b);
+    for (Group& g : b->groups) free_tiles(g);
+    b->groups.clear();
+    const int n = (int)b->members.size();
+    b->seen.resize(n);
+    b->table.resize(n);
+    auto group_of = [&](int Q, int solids, const KParams& phys) -> Group& {
+        for (Group& g : b->groups)
+            if (g.Q == Q && g.solids == solids && std::memcmp(&g.phys, &phys, sizeof(KParams)) == 0) return g;
+        Group g;
+        g.Q = Q;
+        g.solids = solids;
+        g.phys = phys;
+        b->groups.push_back(g);
+        return b->groups.back();
+    };
+    for (int i = 0; i < n; ++i) {
+        const lbm_ctx* c = b->members[i];
+        std::memcpy(&b->seen[i], &c->kp, sizeof(KParams));
+        b->table[i] = dom_of(c);
+        const KParams phys = physics_of(c->kp);
+        const bool walls_only = c->nbmask == nullptr && (c->kp.wall_x || c->kp.wall_y || c->kp.wall_z);
+        if (walls_only) group_of(c->Q, 0, phys).members.push_back(i);
+        group_of(c->Q, has_solid_work(c) ? 1 : 0, phys).members.push_back(i);
+    }
+    for (Group& g : b->groups) {
+        lbm_status s = build_tiles(b, g);
+        if (s != LBM_OK) return s;
+    }
+    return LBM_OK;
+}
+
+// Has any member changed (re-initialised with another solid mask) since the groups were built?
+bool members_changed(const lbm_batch* b) {
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        const BatchDom d = dom_of(b->members[i]);
+        if (std::memcmp(&b->seen[i], &b->members[i]->kp, sizeof(KParams)) != 0 ||
+            std::memcmp(&b->table[i], &d, sizeof(BatchDom)) != 0)
+            return true;
+    }
+    return false;
 }
 
 // One step of every member, starting at AA phase `parity` (psi of the current state valid).
 cudaError_t step_once(lbm_batch* b, int parity, cudaStream_t st) {
     for (const Group& g : b->groups) {
-        cudaError_t e = collide_group(b, g, parity, st);
+        cudaError_t e = collide_group(g, parity, st);
         if (e != cudaSuccess) return e;
     }
     for (const Group& g : b->groups) {
-        cudaError_t e = psi_group(b, g, parity ^ 1, st);
+        cudaError_t e = psi_group(g, parity ^ 1, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -239,36 +384,12 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, 
     lbm_batch* b = new lbm_batch();
     b->members.assign(ctxs, ctxs + n);
     b->stream = (cudaStream_t)cuda_stream;
-    for (int i = 0; i < n; ++i) {
-        const lbm_ctx* c = ctxs[i];
-        const int solids = has_solid_work(c) ? 1 : 0, mp = c->kp.multiphase ? 1 : 0;
-        auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const Group& g) {
-            return g.Q == c->Q && g.solids == solids && g.multiphase == mp;
-        });
-        if (it == b->groups.end()) {
-            Group g;
-            g.Q = c->Q;
-            g.solids = solids;
-            g.multiphase = mp;
-            b->groups.push_back(g);
-            it = b->groups.end() - 1;
-        }
-        it->members.push_back(i);
-    }
-    b->table.resize(n);
-    for (int i = 0; i < n; ++i) b->table[i] = ctxs[i]->kp;
     lbm_status s = LBM_OK;
-    cudaError_t e = cudaMalloc((void**)&b->doms, n * sizeof(KParams));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->counter, sizeof(int));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->doms, b->table.data(), n * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) s = bfail(nullptr, LBM_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
-    for (size_t k = 0; s == LBM_OK && k < b->groups.size(); ++k) {
-        s = build_tiles(b, b->groups[k]);
-        if (s != LBM_OK) lbm::set_thread_error(b->err.c_str());
-    }
+    if (cudaMalloc((void**)&b->counter, sizeof(int)) != cudaSuccess) s = bfail(b, LBM_ERR_OOM, "batch set-up: counter");
+    if (s == LBM_OK) s = regroup(b);
+    if (s == LBM_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) s = bfail(b, LBM_ERR_CUDA, "batch set-up");
     if (s != LBM_OK) {
+        lbm::set_thread_error(b->err.c_str());
         lbm_batch_destroy(b);
         return s;
     }
@@ -280,19 +401,14 @@ lbm_status lbm_batch_step(lbm_batch* b, int32_t n) {
     if (!b) return LBM_ERR_ARG;
     if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
     const int parity = b->members[0]->parity;
-    bool changed = false;
-    for (size_t i = 0; i < b->members.size(); ++i) {
-        const lbm_ctx* c = b->members[i];
+    for (const lbm_ctx* c : b->members) {
         if (c->parity != parity) return bfail(b, LBM_ERR_STATE, "members were stepped apart: AA phases differ");
         if (c->sticky != LBM_OK) return bfail(b, c->sticky, "a member has a sticky error: " + c->err);
-        if (memcmp(&b->table[i], &c->kp, sizeof(KParams)) != 0) {
-            b->table[i] = c->kp;
-            changed = true;
-        }
     }
-    if (changed)   // a member was re-initialised (e.g. its solid mask moved): refresh the device table
-        BCK(b, cudaMemcpyAsync(b->doms, b->table.data(), b->table.size() * sizeof(KParams), cudaMemcpyHostToDevice,
-                               b->stream));
+    if (members_changed(b)) {   // e.g. a member was re-initialised with a solid mask: regroup
+        lbm_status s = regroup(b);
+        if (s != LBM_OK) return s;
+    }
     int done = 0;
     if (n >= 2) {
         if (b->graph_parity != parity) {
@@ -354,10 +470,10 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out
         for (int s = 0; s < trial_steps && e == cudaSuccess; ++s) {
             for (size_t k = 0; k < G && e == cudaSuccess; ++k) {
                 e = cudaEventRecord(ev[2 * (s * G + k)], b->stream);
-                if (e == cudaSuccess) e = collide_group(b, b->groups[k], parity, b->stream);
+                if (e == cudaSuccess) e = collide_group(b->groups[k], parity, b->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(ev[2 * (s * G + k) + 1], b->stream);
             }
-            for (size_t k = 0; k < G && e == cudaSuccess; ++k) e = psi_group(b, b->groups[k], parity ^ 1, b->stream);
+            for (size_t k = 0; k < G && e == cudaSuccess; ++k) e = psi_group(b->groups[k], parity ^ 1, b->stream);
             parity ^= 1;
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -405,10 +521,9 @@ lbm_status lbm_batch_info(const lbm_batch* b, int32_t* ngroups, int32_t* ntiles,
 
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
-    if (b->stream || b->doms) (void)cudaStreamSynchronize(b->stream);
+    (void)cudaStreamSynchronize(b->stream);
     drop_graph(b);
     for (Group& g : b->groups) free_tiles(g);
-    if (b->doms) cudaFree(b->doms);
     if (b->counter) cudaFree(b->counter);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;

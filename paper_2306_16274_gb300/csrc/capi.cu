@@ -242,8 +242,6 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         for (int i = 0; i < c->Q; ++i) c->kp.fq[i] = c->f + (size_t)i * plane;
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
-    c->kp.psi = c->psi;
-    c->kp.status = c->status;
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
     if (e == cudaSuccess) e = alloc((void**)&c->sums, 4 * sizeof(double));
     if (e == cudaSuccess) e = alloc((void**)&c->staging, (size_t)stage_w * n * sizeof(float));
@@ -290,7 +288,6 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->bytes -= n * sizeof(uint32_t);
         c->nbmask = nullptr;
     }
-    c->kp.nbmask = c->nbmask;
     CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream)
                      : lbm::launch_init_q27(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream));
     c->parity = 0;

@@ -15,25 +15,38 @@ constexpr int Q = LBM_Q;
 // ---- density + psi pass (Sec. II A, Sec. II C): one thread per cell, x fastest
 constexpr int PSI_BX = 32, PSI_BY = 4;
 
-// cells (x, y, z) for z in [z0, z1) of one column
-template <int PARITY, bool SOLIDS>
-__device__ __forceinline__ void psi_column(const KParams& kp, const float* __restrict__ f, float* __restrict__ psi,
+// cells (x, y, z) for z in [z0, z1) of one column: pull the populations (AA phase PARITY),
+// rho = sum f, psi from the equation of state
+template <int PARITY, bool SOLIDS, class GM, class A>
+__device__ __forceinline__ void psi_column(const KParams& kp, const GM& g, const A& addr, float* __restrict__ psi,
                                            const uint32_t* __restrict__ nbmask, unsigned* status, int x, int y,
                                            int z0, int z1) {
-    if (x >= kp.nx || y >= kp.ny) return;
+    const int nx = g.nx(), ny = g.ny(), nz = g.nz();
+    if (x >= nx || y >= ny) return;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    Off32 o;
+    o.xo[0] = (uint32_t)wrap1(x - 1, nx);
+    o.xo[1] = (uint32_t)x;
+    o.xo[2] = (uint32_t)wrap1(x + 1, nx);
+    o.yo[0] = (uint32_t)wrap1(y - 1, ny) * (uint32_t)nx;
+    o.yo[1] = (uint32_t)y * (uint32_t)nx;
+    o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
     for (int z = z0; z < z1; ++z) {
-        const Cell c = make_cell(kp, x, y, z);
-        const uint32_t bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
+        o.zo[0] = (uint32_t)wrap1(z - 1, nz) * nxy;
+        o.zo[1] = (uint32_t)z * nxy;
+        o.zo[2] = (uint32_t)wrap1(z + 1, nz) * nxy;
+        o.c = o.zo[1] + o.yo[1] + o.xo[1];
+        const uint32_t bits = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z) : 0u;
         if (bits & 1u) {
-            psi[c.idx] = 0.0f;
+            psi[o.c] = 0.0f;
             continue;
         }
         float p[Q];
-        gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+        gather32<Q, PARITY, SOLIDS>(addr, o, bits, p);
         float rho = 0.0f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) rho += p[i];
-        psi[c.idx] = eval_psi(kp, rho, status);
+        psi[o.c] = eval_psi(kp, rho, status);
     }
 }
 
@@ -42,28 +55,25 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
                                                             float* __restrict__ psi,
                                                             const uint32_t* __restrict__ nbmask,
                                                             unsigned* status) {
-    psi_column<PARITY, SOLIDS>(kp, f, psi, nbmask, status, blockIdx.x * PSI_BX + threadIdx.x,
+    (void)f;   // addressed through kp.fq
+    const KGeom g{kp};
+    const PlanePtrs addr{kp};
+    psi_column<PARITY, SOLIDS>(kp, g, addr, psi, nbmask, status, blockIdx.x * PSI_BX + threadIdx.x,
                                blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1);
 }
 
-// The block's domain parameters, copied from the domain table into shared memory (read uniformly).
-__device__ __forceinline__ void load_domain(KParams& dst, const KParams* __restrict__ doms, int d) {
-    const unsigned* src = reinterpret_cast<const unsigned*>(doms + d);
-    unsigned* out = reinterpret_cast<unsigned*>(&dst);
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    for (int k = tid; k < (int)(sizeof(KParams) / sizeof(unsigned)); k += blockDim.x * blockDim.y) out[k] = src[k];
-}
-
-// multi-domain density + psi pass: one block per tile of any domain
+// multi-domain density + psi pass: one block per tile of any member of the launch's table;
+// physics by value
 template <int PARITY, bool SOLIDS>
-__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParams* __restrict__ doms,
+__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParams phys,
+                                                                  const __grid_constant__ BatchDomTable tab,
                                                                   const BatchTile* __restrict__ tiles) {
-    __shared__ KParams skp;
     const BatchTile t = tiles[blockIdx.x];
-    load_domain(skp, doms, t.d);
-    __syncthreads();
-    psi_column<PARITY, SOLIDS>(skp, skp.fq[0], skp.psi, skp.nbmask, skp.status, t.x0 + threadIdx.x,
-                               t.y0 + threadIdx.y, t.z0, min(t.z0 + t.zc, skp.nz));
+    const BatchDom& m = tab.d[t.d];
+    const DGeom g{m};
+    const PlaneStride addr{m.base, m.plane};
+    psi_column<PARITY, SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x, t.y0 + threadIdx.y,
+                               t.z0, min(t.z0 + t.zc, m.nz));
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
@@ -117,14 +127,15 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 #define LBM_ZM_PREFETCH 1
 #endif
 
-// One tile: cells [x0, x0+32) x [y0, y0+ZM_BY) marching through planes [z0, z0+zchunk).
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__device__ __forceinline__ void collide_tile(const KParams& kp, const float* __restrict__ psi,
+// One tile: cells [x0, x0+32) x [y0, y0+ZM_BY) marching through planes [z0, z0+zchunk); `addr`
+// locates population planes (PlanePtrs or PlaneStride).
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, class GM, class A>
+__device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
                                              int z0, int zchunk, float (*ring)[ZM_RP]) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x = x0 + tx, y = y0 + ty;
-    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int nx = g.nx(), ny = g.ny(), nz = g.nz();
     const bool act_xy = x < nx && y < ny;
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
     const int zend = min(z0 + zchunk, nz);
@@ -136,8 +147,8 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const float* __r
         const int k = tid + s * ZM_NT;
         int gx = x0 - 1 + k % ZM_RX, gy = y0 - 1 + k / ZM_RX;
         bool ok = k < ZM_RP;
-        if (gx < 0) { ok &= !kp.wall_x; gx += nx; } else if (gx >= nx) { ok &= !kp.wall_x; gx -= nx; }
-        if (gy < 0) { ok &= !kp.wall_y; gy += ny; } else if (gy >= ny) { ok &= !kp.wall_y; gy -= ny; }
+        if (gx < 0) { ok &= !g.wall_x(); gx += nx; } else if (gx >= nx) { ok &= !g.wall_x(); gx -= nx; }
+        if (gy < 0) { ok &= !g.wall_y(); gy += ny; } else if (gy >= ny) { ok &= !g.wall_y(); gy -= ny; }
         ok = ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         gok[s] = ok;
         goff[s] = ok ? (uint32_t)gy * (uint32_t)nx + (uint32_t)gx : 0u;
@@ -152,8 +163,8 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const float* __r
     o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
 
     if (MULTIPHASE) {
-        load_psi_plane(ring[0], psi, z0 - 1, nz, kp.wall_z, nxy, goff, gok, tid);
-        load_psi_plane(ring[1], psi, z0, nz, kp.wall_z, nxy, goff, gok, tid);
+        load_psi_plane(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
     }
 #if LBM_ZM_PREFETCH
     // populations of the first plane, then of plane z+1 while plane z is computed
@@ -161,14 +172,14 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const float* __r
     uint32_t bits_n = 0u;
     if (act_xy) {
         set_plane(o, z0, nz, nxy);
-        bits_n = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z0) : 0u;
-        if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(kp, o, bits_n, pn);
+        bits_n = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z0) : 0u;
+        if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(addr, o, bits_n, pn);
     }
 #endif
     const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
     for (int z = z0, j = 0; z < zend; ++z, ++j) {
         if (MULTIPHASE) {
-            load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, kp.wall_z, nxy, goff, gok, tid);
+            load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
             __syncthreads();
         }
         if (!act_xy) continue;
@@ -179,17 +190,17 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const float* __r
         const uint32_t bits = bits_n;
         if (z + 1 < zend) {
             set_plane(o, z + 1, nz, nxy);
-            bits_n = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z + 1) : 0u;
-            if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(kp, o, bits_n, pn);
+            bits_n = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z + 1) : 0u;
+            if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(addr, o, bits_n, pn);
         }
         set_plane(o, z, nz, nxy);
         if (bits & 1u) continue;
 #else
         set_plane(o, z, nz, nxy);
-        const uint32_t bits = SOLIDS ? solid_bits32<Q>(kp, nbmask, o.c, x, y, z) : 0u;
+        const uint32_t bits = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z) : 0u;
         if (bits & 1u) continue;
         float p[Q];
-        gather32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+        gather32<Q, PARITY, SOLIDS>(addr, o, bits, p);
 #endif
         Forces Fo;
         if (MULTIPHASE) {
@@ -203,7 +214,7 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const float* __r
         float rho, ux, uy, uz;
         collide<Q>(kp, p, Fo, rho, ux, uy, uz);
         if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
-        store32<Q, PARITY, SOLIDS>(kp, o, bits, p);
+        store32<Q, PARITY, SOLIDS>(addr, o, bits, p);
     }
 }
 
@@ -212,20 +223,24 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
                                                                 const uint32_t* __restrict__ nbmask,
                                                                 unsigned* status, int zchunk) {
     __shared__ float ring[4][ZM_RP];
-    collide_tile<PARITY, SOLIDS, MULTIPHASE>(kp, psi, nbmask, status, blockIdx.x * ZM_BX, blockIdx.y * ZM_BY,
-                                             blockIdx.z * zchunk, zchunk, ring);
+    const KGeom g{kp};
+    const PlanePtrs addr{kp};
+    collide_tile<PARITY, SOLIDS, MULTIPHASE>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
+                                             blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring);
 }
 
-// multi-domain collide-stream pass: one block per tile of any domain
+// multi-domain collide-stream pass: one block per tile of any member of the launch's table;
+// physics by value
 template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KParams* __restrict__ doms,
+__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KParams phys,
+                                                                      const __grid_constant__ BatchDomTable tab,
                                                                       const BatchTile* __restrict__ tiles) {
     __shared__ float ring[4][ZM_RP];
-    __shared__ KParams skp;
     const BatchTile t = tiles[blockIdx.x];
-    load_domain(skp, doms, t.d);
-    __syncthreads();
-    collide_tile<PARITY, SOLIDS, MULTIPHASE>(skp, skp.psi, skp.nbmask, skp.status, t.x0, t.y0, t.z0, t.zc, ring);
+    const BatchDom& m = tab.d[t.d];
+    const DGeom g{m};
+    const PlaneStride addr{m.base, m.plane};
+    collide_tile<PARITY, SOLIDS, MULTIPHASE>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc, ring);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -456,32 +471,34 @@ cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int 
     }
 }
 
-cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams* doms, const BatchTile* tiles, int ntiles,
-                                                   int parity, int solids, int multiphase, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,
+                                                   const BatchTile* tiles, int ntiles, int parity, int solids,
+                                                   cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     const dim3 b(ZM_BX, ZM_BY);
-    const int key = parity * 4 + (solids ? 2 : 0) + (multiphase ? 1 : 0);
+    const int key = parity * 4 + (solids ? 2 : 0) + (phys.multiphase ? 1 : 0);
     switch (key) {
-        case 0: collide_batch_kernel<0, false, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 1: collide_batch_kernel<0, false, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 2: collide_batch_kernel<0, true, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 3: collide_batch_kernel<0, true, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 4: collide_batch_kernel<1, false, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 5: collide_batch_kernel<1, false, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        case 6: collide_batch_kernel<1, true, false><<<ntiles, b, 0, st>>>(doms, tiles); break;
-        default: collide_batch_kernel<1, true, true><<<ntiles, b, 0, st>>>(doms, tiles); break;
+        case 0: collide_batch_kernel<0, false, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 1: collide_batch_kernel<0, false, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 2: collide_batch_kernel<0, true, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 3: collide_batch_kernel<0, true, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 4: collide_batch_kernel<1, false, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 5: collide_batch_kernel<1, false, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 6: collide_batch_kernel<1, true, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        default: collide_batch_kernel<1, true, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams* doms, const BatchTile* tiles, int ntiles, int parity,
-                                               int solids, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,
+                                               const BatchTile* tiles, int ntiles, int parity, int solids,
+                                               cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     const dim3 b(PSI_BX, PSI_BY);
-    if (parity == 0 && !solids) psi_batch_kernel<0, false><<<ntiles, b, 0, st>>>(doms, tiles);
-    else if (parity == 0) psi_batch_kernel<0, true><<<ntiles, b, 0, st>>>(doms, tiles);
-    else if (!solids) psi_batch_kernel<1, false><<<ntiles, b, 0, st>>>(doms, tiles);
-    else psi_batch_kernel<1, true><<<ntiles, b, 0, st>>>(doms, tiles);
+    if (parity == 0 && !solids) psi_batch_kernel<0, false><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else if (parity == 0) psi_batch_kernel<0, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else if (!solids) psi_batch_kernel<1, false><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else psi_batch_kernel<1, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
     return cudaGetLastError();
 }
 

@@ -311,13 +311,34 @@ struct Off32 {
     __device__ __forceinline__ uint32_t nb(int dx, int dy, int dz) const { return zo[dz + 1] + yo[dy + 1] + xo[dx + 1]; }
 };
 
-template <int Q>
-__device__ __forceinline__ uint32_t solid_bits32(const KParams& kp, const uint32_t* __restrict__ nbmask, uint32_t c,
+// Geometry accessors: the domain's extents and wall flags, read from the kernel parameters
+// (single-domain launches) or from the block's member record in shared memory (multi-domain).
+struct KGeom {
+    const KParams& k;
+    __device__ __forceinline__ int nx() const { return k.nx; }
+    __device__ __forceinline__ int ny() const { return k.ny; }
+    __device__ __forceinline__ int nz() const { return k.nz; }
+    __device__ __forceinline__ int wall_x() const { return k.wall_x; }
+    __device__ __forceinline__ int wall_y() const { return k.wall_y; }
+    __device__ __forceinline__ int wall_z() const { return k.wall_z; }
+};
+struct DGeom {
+    const BatchDom& d;
+    __device__ __forceinline__ int nx() const { return d.nx; }
+    __device__ __forceinline__ int ny() const { return d.ny; }
+    __device__ __forceinline__ int nz() const { return d.nz; }
+    __device__ __forceinline__ int wall_x() const { return d.wall_x; }
+    __device__ __forceinline__ int wall_y() const { return d.wall_y; }
+    __device__ __forceinline__ int wall_z() const { return d.wall_z; }
+};
+
+template <int Q, class GM>
+__device__ __forceinline__ uint32_t solid_bits32(const GM& g, const uint32_t* __restrict__ nbmask, uint32_t c,
                                                  int x, int y, int z) {
     uint32_t bits = nbmask ? __ldg(nbmask + c) : 0u;
-    const bool xl = kp.wall_x && x == 0, xh = kp.wall_x && x == kp.nx - 1;
-    const bool yl = kp.wall_y && y == 0, yh = kp.wall_y && y == kp.ny - 1;
-    const bool zl = kp.wall_z && z == 0, zh = kp.wall_z && z == kp.nz - 1;
+    const bool xl = g.wall_x() && x == 0, xh = g.wall_x() && x == g.nx() - 1;
+    const bool yl = g.wall_y() && y == 0, yh = g.wall_y() && y == g.ny() - 1;
+    const bool zl = g.wall_z() && z == 0, zh = g.wall_z() && z == g.nz() - 1;
     if (xl | xh | yl | yh | zl | zh) {
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
@@ -329,30 +350,44 @@ __device__ __forceinline__ uint32_t solid_bits32(const KParams& kp, const uint32
     return bits;
 }
 
-template <int Q, int PARITY, bool SOLIDS>
-__device__ __forceinline__ void gather32(const KParams& kp, const Off32& o, uint32_t bits, float (&p)[Q]) {
+// Addressing of population plane i: per-plane base pointers from the kernel parameters
+// (constant bank, free operands) for single-domain launches ...
+struct PlanePtrs {
+    const KParams& kp;
+    __device__ __forceinline__ float* plane(int i) const { return kp.fq[i]; }
+};
+// ... or one base pointer and the plane stride in registers for multi-domain launches, whose
+// parameters come from memory (27 pointer loads per access pattern would cost issue slots).
+struct PlaneStride {
+    float* base;
+    long long stride;
+    __device__ __forceinline__ float* plane(int i) const { return base + i * stride; }
+};
+
+template <int Q, int PARITY, bool SOLIDS, class A>
+__device__ __forceinline__ void gather32(const A& a, const Off32& o, uint32_t bits, float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            p[i] = __ldg(kp.fq[i] + o.c);
+            p[i] = __ldg(a.plane(i) + o.c);
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
-            p[i] = __ldg(kp.fq[i] + o.c);
+            p[i] = __ldg(a.plane(i) + o.c);
         } else {
-            p[i] = __ldg(kp.fq[OPP(i)] + o.nb(-EX(i), -EY(i), -EZ(i)));
+            p[i] = __ldg(a.plane(OPP(i)) + o.nb(-EX(i), -EY(i), -EZ(i)));
         }
     }
 }
 
-template <int Q, int PARITY, bool SOLIDS>
-__device__ __forceinline__ void store32(const KParams& kp, const Off32& o, uint32_t bits, const float (&p)[Q]) {
+template <int Q, int PARITY, bool SOLIDS, class A>
+__device__ __forceinline__ void store32(const A& a, const Off32& o, uint32_t bits, const float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            kp.fq[OPP(i)][o.c] = p[i];
+            a.plane(OPP(i))[o.c] = p[i];
         } else if (SOLIDS && ((bits >> i) & 1u)) {
-            kp.fq[OPP(i)][o.c] = p[i];
+            a.plane(OPP(i))[o.c] = p[i];
         } else {
-            kp.fq[i][o.nb(EX(i), EY(i), EZ(i))] = p[i];
+            a.plane(i)[o.nb(EX(i), EY(i), EZ(i))] = p[i];
         }
     }
 }

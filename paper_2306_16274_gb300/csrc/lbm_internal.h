@@ -40,13 +40,27 @@ struct KParams {
     float gx, gy, gz;             // body force per unit mass
     float* fq[27];                // base of population plane i (f + i * plane); cells < 2^31
     int zchunk;                   // z planes per collide block (0 = automatic)
-    // device buffers of the domain (used by the multi-domain kernels, which read KParams from memory)
+};
+
+// Geometry and device buffers of one member of a multi-domain launch (its physics come from the
+// group's KParams, passed by value).
+struct BatchDom {
+    int nx, ny, nz, wall_x, wall_y, wall_z;
+    long long plane;
+    float* base;                  // population plane 0; plane i at base + i * plane
     float* psi;
     const uint32_t* nbmask;
     unsigned* status;
 };
 
-// One block of a multi-domain launch: domain d, cells [x0, x0+32) x [y0, y0+tile height)
+// Members of one multi-domain launch.  The table travels in the kernel parameters (constant bank),
+// so a block's member addresses are read like the single-domain kernel's plane pointers.
+constexpr int BATCH_LAUNCH_DOMS = 64;
+struct BatchDomTable {
+    BatchDom d[BATCH_LAUNCH_DOMS];
+};
+
+// One block of a multi-domain launch: member d of the launch's table, cells [x0, x0+32) x [y0, y0+tile height)
 // x [z0, z0+zc) (clipped to the domain).
 struct BatchTile {
     int d, x0, y0, z0, zc;
@@ -67,10 +81,12 @@ struct BatchTile {
                                     double* partials, int* nblocks, cudaStream_t st);               \
     cudaError_t launch_gather_q##Q(const KParams& kp, int parity, int solids, const float* f,       \
                                    const uint32_t* nbmask, float* out, cudaStream_t st);              \
-    cudaError_t launch_collide_batch_q##Q(const KParams* doms, const BatchTile* tiles, int ntiles,   \
-                                          int parity, int solids, int multiphase, cudaStream_t st);  \
-    cudaError_t launch_psi_batch_q##Q(const KParams* doms, const BatchTile* tiles, int ntiles,       \
-                                      int parity, int solids, cudaStream_t st);                      \
+    cudaError_t launch_collide_batch_q##Q(const KParams& phys, const BatchDomTable& tab,             \
+                                          const BatchTile* tiles, int ntiles, int parity, int solids,  \
+                                          cudaStream_t st);                                           \
+    cudaError_t launch_psi_batch_q##Q(const KParams& phys, const BatchDomTable& tab,                 \
+                                      const BatchTile* tiles, int ntiles, int parity, int solids,      \
+                                      cudaStream_t st);                                               \
     int tile_height_q##Q();                                                                         \
     int resident_blocks_q##Q();
 

@@ -55,7 +55,9 @@ def test_batch_equals_members_stepped_alone(nsteps):
     b.step(nsteps)
     b.sync()
     info = b.info()
-    assert info["groups"] == 5
+    # groups: one per (lattice, solid handling, physics); the walled droplet without interior
+    # solids has its interior tiles in a plain group and its boundary tiles in a solid group
+    assert info["groups"] == 7
     if nsteps >= 2:
         assert info["graph_mode"] in (1, 2)
     for a, t in zip(alone, together):
@@ -118,4 +120,37 @@ def test_batch_rejects_mixed_phases_and_duplicates():
     with pytest.raises(LBMError) as e:
         b.step(2)
     assert e.value.status == 7
+    b.close()
+
+
+def test_batch_groups_share_physics_and_regroup_on_new_mask():
+    # members with equal physics share one launch per pass, whatever their shapes; a member
+    # re-initialised with a solid mask moves to a solid-handling group at the next step
+    from paper_2306_16274_gb300 import Batch
+    kw7, rl7, rv7 = U.cs_eos("T0.7")
+    m = []
+    for shape, r in (((37, 21, 18), 6.0), ((40, 33, 20), 7.0), ((16, 16, 16), 4.0)):
+        m.append((dict(lattice=19, shape=shape, sigma=0.1, kappa=0.3, **kw7), *W.droplet(shape, r, rl7, rv7), None))
+    alone = _make(m)
+    together = _make(m)
+    b = Batch(together)
+    assert b.info()["groups"] == 1
+    b.step(4)                                   # even: re-initialising restarts at AA phase 0
+    for a in alone:
+        a.step(4)
+    d, _, _, _ = m[1]
+    rho, u = W.droplet(d["shape"], 7.0, rl7, rv7)
+    solid = W.cylinder_mask(d["shape"], 3.0, axis="z")
+    import torch
+    for s in (alone[1], together[1]):
+        s.init_fields(torch.tensor(rho, dtype=torch.float32, device="cuda"),
+                      torch.tensor(u, dtype=torch.float32, device="cuda"),
+                      torch.tensor(solid, dtype=torch.uint8, device="cuda"))
+    b.step(6)
+    b.sync()
+    assert b.info()["groups"] == 2
+    for a in alone:
+        a.step(6)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
     b.close()
