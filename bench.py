@@ -327,6 +327,89 @@ def run_batched(steps, n_jobs=64):
             "speedup": loop_ms / batch_ms}
 
 
+# ---------------------------------------------------------------- serving (continuous batching)
+SERVE_WORKLOAD = ("request stream of {n} jobs (numpy seed 2306): by fair coin droplet impact on a wall with a cylinder "
+                  "(Sec. IV B; edge L ~ U{{64..160}}, R0 = L/6, R/R0 ~ U[0.2, 2], cylinder on the bottom wall along y, "
+                  "walls in z, G_ads = 0.23, We = 10 from the oracle's Laplace surface tension, nu = 0.05, tanh width 3, "
+                  "run until "
+                  "the droplet leaves the solid or 4 capillary times) or a static droplet of a kappa sweep "
+                  "(periodic L^3, R ~ U[L/8, L/4], kappa in 0..0.6, 2000 steps); lattice D3Q19/D3Q27 by fair coin; "
+                  "C-S at 0.7 T_c, sigma = 0.1; ticks of 100 steps; budget 150 GB")
+
+
+def serving_specs(n_jobs, rate, seed=2306):
+    """JobSpecs of the serving workload, arrivals Poisson with `rate` per second (0: all at once).
+    Fields are generated once here (the client's side of a request) and handed over as float32."""
+    from paper_2306_16274_gb300 import Params
+    from paper_2306_16274_gb300.serve import JobSpec
+    c = W.constants()["cs"]
+    t = c["T0.7"]
+    rl, rv = t["rho_l"], t["rho_v"]
+    gamma = c["gamma_T0.7"]["kappa0.3"]
+    eos = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1)
+    specs = []
+    for k, j in enumerate(W.serving_jobs(n_jobs, rate, seed=seed)):
+        if j["kind"] == "impact":
+            R0 = j["R0"]
+            U = (10.0 * gamma / (rl * R0)) ** 0.5            # We = rho_l R0 U^2 / gamma = 10
+            tau = (rl * R0 ** 3 / gamma) ** 0.5              # capillary time of Sec. III E
+            p = Params(lattice=j["lattice"], shape=j["shape"], bc=("periodic", "periodic", "wall"), kappa=0.3,
+                       G_ads=0.23, rates={"s2": 1.0 / (3 * 0.05 + 0.5)}, **eos)
+            rho, u, solid = W.cylinder_impact(j["shape"], R0, j["Rc"], rl, rv, U, gap=3.0, W=3.0)
+            f = (rho.astype(np.float32), u.astype(np.float32), solid)
+            specs.append(JobSpec(name=j["name"], params=p, make_fields=lambda f=f: f, steps=int(4 * tau),
+                                 stop_on_detach=True, threshold=0.5 * (rl + rv), arrival=j["arrival"],
+                                 has_solid=True))
+        else:
+            p = Params(lattice=j["lattice"], shape=j["shape"], kappa=0.15 * (k % 5), **eos)
+            rho, u = W.droplet(j["shape"], j["R"], rl, rv)
+            f = (rho.astype(np.float32), u.astype(np.float32), None)
+            specs.append(JobSpec(name=j["name"], params=p, make_fields=lambda f=f: f, steps=2000,
+                                 arrival=j["arrival"]))
+    return specs
+
+
+def run_serving(n_jobs=24, load=0.8, tick=100, budget=150e9):
+    """The request stream served one job at a time (single-domain kernels) and with continuous
+    batching: first all requests at t = 0 (throughput), then Poisson arrivals at `load` times the
+    one-at-a-time service rate measured in the first run (time-to-result)."""
+    import torch
+
+    from paper_2306_16274_gb300.serve import GpuEngine, Server, summary
+
+    def serve(specs, batched):
+        eng = GpuEngine(batched=batched)
+        srv = Server(eng, budget, tick=tick, max_active=64 if batched else 1)
+        res = srv.run(specs)
+        eng.close()
+        torch.cuda.synchronize()
+        out = summary(res, srv.stats)
+        out["failed"] = [r.name + ": " + r.status for r in res if r.status != "ok"]
+        return out, res
+
+    closed = serving_specs(n_jobs, 0.0)
+    seq_c, seq_res = serve(closed, False)
+    bat_c, bat_res = serve(closed, True)
+    same = all(a.steps == b.steps and a.touch == b.touch and a.detach == b.detach and a.sums == b.sums
+               for a, b in zip(seq_res, bat_res))
+    rate = load * n_jobs / seq_c["busy_s"]
+    open_ = serving_specs(n_jobs, rate)
+    seq_o, _ = serve(open_, False)
+    bat_o, _ = serve(open_, True)
+    keep = ("p50_s", "p99_s", "mean_s", "wall_s", "busy_s", "mlups_busy", "mlups_wall", "peak_active", "peak_bytes",
+            "ok", "failed")
+    tc = [r.contact_steps for r in bat_res if r.contact_steps is not None]
+    return {"workload": SERVE_WORKLOAD.format(n=n_jobs), "jobs": n_jobs, "cell_steps": seq_c["cell_steps"],
+            "results_equal_alone_and_batched": same,
+            "all_at_once": {"one_at_a_time": {k: seq_c[k] for k in keep},
+                            "batched": {k: bat_c[k] for k in keep},
+                            "mlups_ratio": bat_c["mlups_wall"] / seq_c["mlups_wall"]},
+            "poisson": {"rate_per_s": rate, "load": load,
+                        "one_at_a_time": {k: seq_o[k] for k in keep}, "batched": {k: bat_o[k] for k in keep},
+                        "p50_ratio": seq_o["p50_s"] / bat_o["p50_s"], "p99_ratio": seq_o["p99_s"] / bat_o["p99_s"]},
+            "impacts_detached": len(tc)}
+
+
 # ---------------------------------------------------------------- oracle timing on host cores
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -419,6 +502,8 @@ def main():
     ap.add_argument("--no-q27", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=24)
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
@@ -452,6 +537,7 @@ def main():
     r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
     e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
     batched = None if (args.no_batched or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
+    serving = None if (args.no_serving or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
     if rank != 0:
         return
     ab = algorithmic_bytes(19)
@@ -491,6 +577,8 @@ def main():
         line["e2e"] = e2e
     if batched:
         line["batched"] = batched
+    if serving:
+        line["serving"] = serving
     if ws == 1 and not args.no_cpu_baseline:
         try:
             cb = oracle_timing(19, args.cpu_seconds)

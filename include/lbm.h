@@ -50,6 +50,9 @@ extern "C" {
 
 #define LBM_ABI_VERSION 1
 
+/* Largest nx, ny or nz: the density/psi pass launches one block row per z plane. */
+#define LBM_MAX_EXTENT 65535
+
 typedef struct lbm_ctx lbm_ctx;
 
 typedef enum {
@@ -81,7 +84,7 @@ enum {
 
 typedef struct {
     int32_t lattice;        /* 19 (App. C) or 27 (Sec. II)                                   */
-    int32_t nx, ny, nz;     /* cells per axis, each >= 1                                     */
+    int32_t nx, ny, nz;     /* cells per axis, 1 .. LBM_MAX_EXTENT, nx ny nz < 2^31          */
     int32_t bc[3];          /* LBM_BC_* for x, y, z                                          */
     int32_t eos;            /* LBM_EOS_*                                                     */
     double eos_p[5];        /* EOS parameters, see above                                     */
@@ -166,8 +169,36 @@ lbm_status lbm_get_kernel_timing(lbm_ctx* ctx, double ms[2], int64_t launches[2]
 /* Number of steps taken since lbm_init_fields (or -1 for a NULL context). */
 int64_t lbm_step_count(const lbm_ctx* ctx);
 
-/* Total device bytes the context holds. */
+/* Total device bytes the context holds.  Calls with host pointers
+ * (ptrs_on_device = 0) add a staging buffer on first use -- 4 floats per cell
+ * for fields, Q per cell for populations -- that is kept until lbm_destroy. */
 size_t lbm_device_bytes(const lbm_ctx* ctx);
+
+/* Device bytes a context created from *params holds after lbm_init_fields
+ * with device pointers (with_solid != 0: with a solid mask), without creating
+ * it: the populations (Q planes padded to 64 cells), psi, the status word and
+ * the reduction scratch, plus 5 bytes per cell for a mask.  For admission
+ * control under a memory budget; the paper has no counterpart.  Errors: as
+ * lbm_create's validation (LBM_ERR_ARG), bytes == NULL. */
+lbm_status lbm_estimate_bytes(const lbm_params* params, int32_t with_solid, size_t* bytes);
+
+/* Contact detector for droplet impact (Sec. III E: contact time; Sec. IV B:
+ * contact time on a wall with a cylinder).  A fluid cell is liquid when its
+ * rho (formed as lbm_get_moments forms it) exceeds rho_threshold (the text
+ * defines liquid and contact in words; the usual reading is the mid-density
+ * (rho_l + rho_v) / 2).  Writes six int32:
+ *   out[0] liquid fluid cells with at least one solid lattice neighbour
+ *          (an interior solid cell or a wall plane);
+ *   out[1] liquid cells in the first layer above a bottom wall (z = 0, only
+ *          when z has walls), the spreading footprint;
+ *   out[2], out[3] min and max x of those floor cells (INT32_MAX, INT32_MIN
+ *          when there are none); out[4], out[5] the same for y.
+ * ptrs_on_device != 0: `out` is device memory; the call only enqueues on the
+ * context's stream (so many contexts can write into one buffer and be read
+ * with one copy).  0: host memory; the call synchronises and returns the
+ * status as lbm_sync does.  Domains without walls or solids report 0 contacts.
+ * The paper has no such entry point; it reads contact from its snapshots. */
+lbm_status lbm_contact(lbm_ctx* ctx, float rho_threshold, int32_t* out, int ptrs_on_device);
 
 /* Frees the device state.  Waits for the stream first.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);

@@ -3,6 +3,6 @@
 The compute path is liblbm.so (hand-written CUDA for sm_103a behind the C ABI in
 include/lbm.h); ``lbm`` is its Python binding.
 """
-from .lbm import Batch, LBMError, Params, Simulation, lib  # noqa: F401
+from .lbm import CONTACT_FIELDS, Batch, LBMError, Params, Simulation, estimate_bytes, lib  # noqa: F401
 
-__all__ = ["Batch", "LBMError", "Params", "Simulation", "lib"]
+__all__ = ["CONTACT_FIELDS", "Batch", "LBMError", "Params", "Simulation", "estimate_bytes", "lib"]

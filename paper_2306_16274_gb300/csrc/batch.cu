@@ -33,8 +33,7 @@ constexpr int PSI_TILE_H = 4;   // rows of the density/psi tiles (its blocks are
 // tile arrays.
 struct Launch {
     BatchDomTable tab{};
-    int t0 = 0, nt = 0;             // collide tiles
-    int p0 = 0, np = 0;             // density/psi tiles
+    int t0 = 0, nt = 0;             // tiles (both passes)
 };
 
 struct Group {
@@ -43,10 +42,8 @@ struct Group {
     std::vector<int> members;       // members with tiles in this group
     int zchunk = 0;                 // 0 = automatic
     std::vector<Launch> launches;
-    BatchTile* tiles = nullptr;     // collide tiles (device)
+    BatchTile* tiles = nullptr;     // tiles of both passes (device)
     int ntiles = 0;
-    BatchTile* ptiles = nullptr;    // density/psi tiles (device)
-    int nptiles = 0;
 };
 
 __global__ void set_counter_kernel(int* counter, int value) { *counter = value; }
@@ -100,6 +97,9 @@ struct lbm_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_parity = -1;          // AA phase the graph was recorded for
     int graph_mode = 0;             // 0 none yet, 1 WHILE conditional node, 2 replayed two-step graph
+    std::vector<cudaStream_t> side; // one per group: the groups of a pass run concurrently
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> done;
     std::string err;
 };
 
@@ -121,9 +121,8 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
 
 void free_tiles(Group& g) {
     if (g.tiles) cudaFree(g.tiles);
-    if (g.ptiles) cudaFree(g.ptiles);
-    g.tiles = g.ptiles = nullptr;
-    g.ntiles = g.nptiles = 0;
+    g.tiles = nullptr;
+    g.ntiles = 0;
     g.launches.clear();
 }
 
@@ -134,88 +133,118 @@ void drop_graph(lbm_batch* b) {
     b->graph_mode = 0;
 }
 
-// Does the x/y column range or the z plane range of a tile touch a wall?  Walls are the planes
-// just outside a wall axis, so only the first and last cells of that axis see them.
-bool tile_touches_wall(const KParams& k, int x0, int w, int y0, int h, int z0, int zc) {
-    return (k.wall_x && (x0 == 0 || x0 + w >= k.nx)) || (k.wall_y && (y0 == 0 || y0 + h >= k.ny)) ||
-           (k.wall_z && (z0 == 0 || z0 + zc >= k.nz));
+constexpr int TILE_W = 32;
+constexpr int ZC_AUTO_MAX = 32;   // automatic z-chunks: longer marches gain little, and in a mix of
+                                  // uneven members shorter blocks balance the last wave
+
+// flags[(z * nyb + yb) * nxb + xb] = 1 if a cell of the 32 x th column (xb, yb) in plane z has a
+// solid neighbour or is solid (its neighbour mask is nonzero).
+__global__ void tile_flags_kernel(const uint32_t* __restrict__ nbmask, int nx, int ny, int th, uint8_t* flags) {
+    const int x = blockIdx.x * TILE_W + threadIdx.x, y = blockIdx.y * th + threadIdx.y, z = blockIdx.z;
+    bool any = false;
+    if (x < nx && y < ny) any = nbmask[((long long)z * ny + y) * nx + x] != 0u;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        flags[((long long)z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = any ? 1 : 0;
 }
 
-// Tiles of the members of a group: 32 x h cells per tile in (x, y), z-chunks chosen so that the
-// whole group gives a few waves of resident blocks (or the group's fixed zchunk).  In a group
-// without solid handling, members whose only solids are domain walls contribute their interior
-// tiles; their wall-touching tiles (with single-plane chunks at z walls) go to the matching
-// solid-handling group, so only the boundary shell pays for the solid tests.
+// Mask flags of a member (cached on the context until its fields are re-initialised).
+lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int th) {
+    const KParams& k = c->kp;
+    const long long nxb = (k.nx + TILE_W - 1) / TILE_W, nyb = (k.ny + th - 1) / th;
+    const size_t n = (size_t)(nxb * nyb * k.nz);
+    if (!c->nbmask || c->tile_flags.size() == n) return LBM_OK;
+    uint8_t* d = nullptr;
+    BCK(b, cudaMalloc((void**)&d, n));
+    c->tile_flags.assign(n, 1);
+    tile_flags_kernel<<<dim3((unsigned)nxb, (unsigned)nyb, (unsigned)k.nz), dim3(TILE_W, th), 0, b->stream>>>(
+        c->nbmask, k.nx, k.ny, th, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->tile_flags.data(), d, n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        c->tile_flags.clear();
+        return bfail(b, LBM_ERR_CUDA, std::string("tile flags: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+// Tiles of the members of a group: 32 x th cells in (x, y) and a run of z planes.  Along every
+// column the planes are split into runs that need solid handling (a cell with a solid neighbour:
+// mask, or the first / last plane, row or column next to a wall) and runs that do not; runs are
+// cut into chunks of at most zc planes, chosen so that the whole group gives a few waves of
+// resident blocks (or the group's fixed zchunk).  A member with solids contributes its solid-free
+// chunks to the group without solid handling and the others to the solid group of its physics,
+// so only cells near solids pay for the solid tests.
 lbm_status build_tiles(lbm_batch* b, Group& g) {
     free_tiles(g);
     const int th = g.Q == 19 ? lbm::tile_height_q19() : lbm::tile_height_q27();
     const int resident = g.Q == 19 ? lbm::resident_blocks_q19() : lbm::resident_blocks_q27();
+    if (th != PSI_TILE_H) return bfail(b, LBM_ERR_STATE, "collide and psi tile heights differ");
     long long cols = 0;
     for (int d : g.members) {
         const KParams& k = b->members[d]->kp;
-        cols += (long long)((k.nx + 31) / 32) * ((k.ny + th - 1) / th);
+        cols += (long long)((k.nx + TILE_W - 1) / TILE_W) * ((k.ny + th - 1) / th);
     }
     const long long target = 152LL * resident * 4;
     const long long chunks_auto = std::max(1LL, (target + cols - 1) / std::max(cols, 1LL));
-    std::vector<BatchTile> t, pt;
+    std::vector<BatchTile> t;
+    std::vector<uint8_t> need;   // per plane of one column: needs solid handling
     for (size_t j = 0; j < g.members.size(); ++j) {
         const int d = (int)(j % lbm::BATCH_LAUNCH_DOMS);   // slot in the launch's member table
         if (d == 0) {
             g.launches.emplace_back();
             g.launches.back().t0 = (int)t.size();
-            g.launches.back().p0 = (int)pt.size();
         }
         Launch& L = g.launches.back();
         L.tab.d[d] = b->table[g.members[j]];
-        const lbm_ctx* c = b->members[g.members[j]];
+        lbm_ctx* c = b->members[g.members[j]];
         const KParams& k = c->kp;
-        const bool walls_only = c->nbmask == nullptr && (k.wall_x || k.wall_y || k.wall_z);
+        const bool solid_work = has_solid_work(c);
+        lbm_status fs = member_tile_flags(b, c, th);
+        if (fs != LBM_OK) return fs;
         int zc;
         if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);
         else {
             const long long ch = std::min<long long>(chunks_auto, k.nz);
-            zc = (int)((k.nz + ch - 1) / ch);
+            zc = std::min(ZC_AUTO_MAX, (int)((k.nz + ch - 1) / ch));
         }
-        // z-chunk boundaries: single planes at z walls, zc-plane chunks in between
-        std::vector<std::pair<int, int>> zr;
-        int zlo = 0, zhi = k.nz;
-        if (walls_only && k.wall_z) {
-            zr.push_back({0, 1});
-            if (k.nz > 1) zr.push_back({k.nz - 1, 1});
-            zlo = 1;
-            zhi = k.nz - 1;
-        }
-        for (int z0 = zlo; z0 < zhi; z0 += zc) zr.push_back({z0, std::min(zc, zhi - z0)});
-        for (const auto& r : zr) {
-            for (int y0 = 0; y0 < k.ny; y0 += th)
-                for (int x0 = 0; x0 < k.nx; x0 += 32) {
-                    const bool wall = tile_touches_wall(k, x0, 32, y0, th, r.first, r.second);
-                    const bool mine = !walls_only || (wall == (g.solids != 0));
-                    if (mine) t.push_back({d, x0, y0, r.first, r.second});
+        const int nxb = (k.nx + TILE_W - 1) / TILE_W, nyb = (k.ny + th - 1) / th;
+        const int member_t0 = (int)t.size() - L.t0;
+        need.resize(k.nz);
+        for (int yb = 0; yb < nyb; ++yb)
+            for (int xb = 0; xb < nxb; ++xb) {
+                const int x0 = xb * TILE_W, y0 = yb * th;
+                const bool side = (k.wall_x && (x0 == 0 || x0 + TILE_W >= k.nx)) ||
+                                  (k.wall_y && (y0 == 0 || y0 + th >= k.ny));
+                for (int z = 0; z < k.nz; ++z) {
+                    bool s = side || (k.wall_z && (z == 0 || z == k.nz - 1));
+                    if (c->nbmask) s = s || c->tile_flags[((size_t)z * nyb + yb) * nxb + xb] != 0;
+                    need[z] = s ? 1 : 0;
                 }
-            for (int y0 = 0; y0 < k.ny; y0 += PSI_TILE_H)
-                for (int x0 = 0; x0 < k.nx; x0 += 32) {
-                    const bool wall = tile_touches_wall(k, x0, 32, y0, PSI_TILE_H, r.first, r.second);
-                    const bool mine = !walls_only || (wall == (g.solids != 0));
-                    if (mine) pt.push_back({d, x0, y0, r.first, r.second});
+                for (int z0 = 0; z0 < k.nz;) {
+                    int z1 = z0 + 1;
+                    while (z1 < k.nz && need[z1] == need[z0] && z1 - z0 < zc) ++z1;
+                    const bool mine = solid_work ? (need[z0] != 0) == (g.solids != 0) : true;
+                    if (mine) t.push_back({d, x0, y0, z0, z1 - z0});
+                    z0 = z1;
                 }
-        }
+            }
+        // z-chunk-major order within the member (as the single-domain grid): blocks resident at
+        // the same time work on neighbouring columns of the same planes
+        std::stable_sort(t.begin() + L.t0 + member_t0, t.end(), [](const BatchTile& a, const BatchTile& b2) {
+            return a.z0 != b2.z0 ? a.z0 < b2.z0 : (a.y0 != b2.y0 ? a.y0 < b2.y0 : a.x0 < b2.x0);
+        });
         L.nt = (int)t.size() - L.t0;
-        L.np = (int)pt.size() - L.p0;
     }
-    if (t.size() > 0x7fffffff || pt.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
+    if (t.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
     if (!t.empty()) {
         BCK(b, cudaMalloc((void**)&g.tiles, t.size() * sizeof(BatchTile)));
         BCK(b, cudaMemcpyAsync(g.tiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
     }
-    if (!pt.empty()) {
-        BCK(b, cudaMalloc((void**)&g.ptiles, pt.size() * sizeof(BatchTile)));
-        BCK(b, cudaMemcpyAsync(g.ptiles, pt.data(), pt.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
-                               b->stream));
-    }
     BCK(b, cudaStreamSynchronize(b->stream));
     g.ntiles = (int)t.size();
-    g.nptiles = (int)pt.size();
     return LBM_OK;
 }
 
@@ -233,9 +262,9 @@ cudaError_t collide_group(const Group& g, int parity, cudaStream_t st) {
 cudaError_t psi_group(const Group& g, int parity, cudaStream_t st) {
     if (!g.phys.multiphase) return cudaSuccess;
     for (const Launch& L : g.launches) {
-        const BatchTile* t = g.ptiles + L.p0;
-        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.np, parity, g.solids, st)
-                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.np, parity, g.solids, st);
+        const BatchTile* t = g.tiles + L.t0;   // the collide tiles (32 x 4 columns, same split)
+        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, st)
+                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -262,12 +291,14 @@ lbm_status regroup(lbm_batch* b) {
     };
     for (int i = 0; i < n; ++i) {
         const lbm_ctx* c = b->members[i];
+        if ((unsigned long long)c->Q * (unsigned long long)c->kp.plane > 0xFFFFFFFFull)
+            return bfail(b, LBM_ERR_ARG, "a batch member holds 2^32 or more population values "
+                                         "(Q x cells rounded up to 64); step it alone");
         std::memcpy(&b->seen[i], &c->kp, sizeof(KParams));
         b->table[i] = dom_of(c);
         const KParams phys = physics_of(c->kp);
-        const bool walls_only = c->nbmask == nullptr && (c->kp.wall_x || c->kp.wall_y || c->kp.wall_z);
-        if (walls_only) group_of(c->Q, 0, phys).members.push_back(i);
-        group_of(c->Q, has_solid_work(c) ? 1 : 0, phys).members.push_back(i);
+        group_of(c->Q, 0, phys).members.push_back(i);   // solid-free tiles
+        if (has_solid_work(c)) group_of(c->Q, 1, phys).members.push_back(i);
     }
     for (Group& g : b->groups) {
         lbm_status s = build_tiles(b, g);
@@ -287,17 +318,42 @@ bool members_changed(const lbm_batch* b) {
     return false;
 }
 
+// One pass (collide-stream or density/psi) of every group.  The groups' launches are
+// independent within a pass -- tiles of one member in two groups touch disjoint cells, and the
+// in-place AA update of a cell reads and writes only that cell's slots -- so they are forked onto
+// one side stream each and joined before the next pass (in a captured graph: parallel nodes
+// between two joins).  The next pass needs all of them: psi reads populations that neighbouring
+// tiles wrote, and collide reads the psi halo.
+cudaError_t pass(lbm_batch* b, bool collide, int parity, cudaStream_t st) {
+    const size_t G = b->groups.size();
+    if (G == 1) return collide ? collide_group(b->groups[0], parity, st) : psi_group(b->groups[0], parity, st);
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && b->side.size() < G) {
+        cudaStream_t s2 = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            b->side.push_back(s2);
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->done.push_back(ev);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
+    for (size_t k = 0; k < G && e == cudaSuccess; ++k) {
+        e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        if (e == cudaSuccess)
+            e = collide ? collide_group(b->groups[k], parity, b->side[k]) : psi_group(b->groups[k], parity, b->side[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done[k], b->side[k]);
+    }
+    for (size_t k = 0; k < G && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(st, b->done[k], 0);
+    return e;
+}
+
 // One step of every member, starting at AA phase `parity` (psi of the current state valid).
 cudaError_t step_once(lbm_batch* b, int parity, cudaStream_t st) {
-    for (const Group& g : b->groups) {
-        cudaError_t e = collide_group(g, parity, st);
-        if (e != cudaSuccess) return e;
-    }
-    for (const Group& g : b->groups) {
-        cudaError_t e = psi_group(g, parity ^ 1, st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    cudaError_t e = pass(b, true, parity, st);
+    return e == cudaSuccess ? pass(b, false, parity ^ 1, st) : e;
 }
 
 lbm_status record_graph(lbm_batch* b, int parity) {
@@ -526,6 +582,9 @@ void lbm_batch_destroy(lbm_batch* b) {
     for (Group& g : b->groups) free_tiles(g);
     if (b->counter) cudaFree(b->counter);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t s2 : b->side) cudaStreamDestroy(s2);
+    for (cudaEvent_t ev : b->done) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 

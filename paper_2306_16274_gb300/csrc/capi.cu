@@ -1,6 +1,7 @@
 // C ABI of liblbm.so (declared in include/lbm.h): context lifetime, parameter
 // validation and derivation, step sequencing (AA parity), host<->device
 // marshalling, status handling and kernel timing.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -37,6 +38,10 @@ lbm_status validate(const lbm_params* p, std::string& why) {
     if (!p) { why = "params is NULL"; return LBM_ERR_ARG; }
     if (p->lattice != 19 && p->lattice != 27) { why = "lattice must be 19 or 27"; return LBM_ERR_ARG; }
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "nx, ny, nz must be >= 1"; return LBM_ERR_ARG; }
+    if (p->nx > LBM_MAX_EXTENT || p->ny > LBM_MAX_EXTENT || p->nz > LBM_MAX_EXTENT) {
+        why = "nx, ny, nz must be <= LBM_MAX_EXTENT (65535)";
+        return LBM_ERR_ARG;
+    }
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (n >= (1LL << 31)) { why = "domain too large: at most 2^31 - 1 cells"; return LBM_ERR_ARG; }
     for (int a = 0; a < 3; ++a)
@@ -194,6 +199,39 @@ lbm_status read_status(lbm_ctx* c) {
 }
 
 // copy helper: device destination or host destination through the stream
+// Host transfers go through one staging buffer, allocated on first use and grown on demand, so
+// a context that is only fed from device memory holds no more than its resident state.
+cudaError_t ensure_staging(lbm_ctx* c, size_t floats) {
+    if (c->staging_floats >= floats) return cudaSuccess;
+    if (c->staging) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        cudaFree(c->staging);
+        c->bytes -= c->staging_floats * sizeof(float);
+        c->staging = nullptr;
+        c->staging_floats = 0;
+    }
+    cudaError_t e = cudaMalloc((void**)&c->staging, floats * sizeof(float));
+    if (e != cudaSuccess) {
+        c->staging = nullptr;
+        return e;
+    }
+    c->staging_floats = floats;
+    c->bytes += floats * sizeof(float);
+    return cudaSuccess;
+}
+
+// Device bytes a context holds once initialised (host staging excluded).
+size_t resident_bytes(const KParams& k, int Q, bool with_solid) {
+    const size_t n = (size_t)k.ncell;
+    size_t b = (size_t)Q * (size_t)k.plane * sizeof(float);   // populations
+    b += n * sizeof(float);                                   // psi
+    b += 64;                                                  // status word
+    b += (size_t)lbm::moments_partial_blocks(k) * 4 * sizeof(double) + 4 * sizeof(double);
+    if (with_solid) b += n * sizeof(uint32_t) + n;            // neighbour mask + solid copy
+    return b;
+}
+
 lbm_status copy_out(lbm_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
     CK(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     return LBM_OK;
@@ -236,7 +274,6 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         return e;
     };
     cudaError_t e = cudaGetDevice(&c->device);
-    const int stage_w = c->Q > 4 ? c->Q : 4;
     if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * sizeof(float));
     if (e == cudaSuccess)
         for (int i = 0; i < c->Q; ++i) c->kp.fq[i] = c->f + (size_t)i * plane;
@@ -244,7 +281,6 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
     if (e == cudaSuccess) e = alloc((void**)&c->sums, 4 * sizeof(double));
-    if (e == cudaSuccess) e = alloc((void**)&c->staging, (size_t)stage_w * n * sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, 64, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->psi, 0, (size_t)n * sizeof(float), c->stream);
     if (e != cudaSuccess) {
@@ -265,6 +301,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
     const float* d_rho = rho;
     const float* d_u = u;
     if (!on_device) {
+        CK(c, ensure_staging(c, 4 * (size_t)n));
         CK(c, cudaMemcpyAsync(c->staging, rho, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaMemcpyAsync(c->staging + n, u, 3 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
         d_rho = c->staging;
@@ -288,6 +325,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->bytes -= n * sizeof(uint32_t);
         c->nbmask = nullptr;
     }
+    c->tile_flags.clear();
     CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream)
                      : lbm::launch_init_q27(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream));
     c->parity = 0;
@@ -327,6 +365,7 @@ lbm_status lbm_get_moments(lbm_ctx* c, float* rho, float* u, double* sums, int o
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_moments before lbm_init_fields");
     const long long n = c->kp.ncell;
+    if (!on_device && (rho || u)) CK(c, ensure_staging(c, 4 * (size_t)n));
     float* d_rho = on_device ? rho : (rho ? c->staging : nullptr);
     float* d_u = on_device ? u : (u ? c->staging + n : nullptr);
     int nb = 0;
@@ -357,6 +396,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int on_device) {
     if (!c || !f) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_populations before lbm_init_fields");
     const long long n = c->kp.ncell;
+    if (!on_device) CK(c, ensure_staging(c, (size_t)c->Q * n));
     float* dst = on_device ? f : c->staging;
     const int s = has_solids(c);
     CK(c, c->Q == 19 ? lbm::launch_gather_q19(c->kp, c->parity, s, c->f, c->nbmask, dst, c->stream)
@@ -407,6 +447,36 @@ int64_t lbm_step_count(const lbm_ctx* c) { return c ? c->t : -1; }
 
 size_t lbm_device_bytes(const lbm_ctx* c) { return c ? c->bytes : 0; }
 
+lbm_status lbm_estimate_bytes(const lbm_params* params, int32_t with_solid, size_t* bytes) {
+    if (!bytes) return fail(nullptr, LBM_ERR_ARG, "bytes is NULL");
+    *bytes = 0;
+    std::string why;
+    lbm_status v = validate(params, why);
+    if (v != LBM_OK) return fail(nullptr, v, why);
+    const long long n = (long long)params->nx * params->ny * params->nz;
+    const KParams k = derive(*params, (n + 63) / 64 * 64);
+    *bytes = resident_bytes(k, params->lattice, with_solid != 0);
+    return LBM_OK;
+}
+
+lbm_status lbm_contact(lbm_ctx* c, float rho_threshold, int32_t* out, int on_device) {
+    if (!c || !out) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_contact before lbm_init_fields");
+    if (!std::isfinite(rho_threshold)) return fail(c, LBM_ERR_ARG, "rho_threshold must be finite");
+    int* d_out = on_device ? reinterpret_cast<int*>(out) : reinterpret_cast<int*>(c->sums);   // sums: 32 bytes
+    CK(c, lbm::launch_contact_init(d_out, c->stream));
+    if (has_solids(c))
+        CK(c, c->Q == 19 ? lbm::launch_contact_q19(c->kp, c->parity, c->f, c->nbmask, rho_threshold, d_out, c->stream)
+                         : lbm::launch_contact_q27(c->kp, c->parity, c->f, c->nbmask, rho_threshold, d_out,
+                                                   c->stream));
+    if (on_device) return LBM_OK;
+    int32_t h[6];
+    CK(c, cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::memcpy(out, h, sizeof(h));
+    return read_status(c);
+}
+
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     if (c->stream || c->f) (void)cudaStreamSynchronize(c->stream);
@@ -453,6 +523,11 @@ __host__ __device__ constexpr int ey27(int i) {
 __host__ __device__ constexpr int ez27(int i) {
     constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
     return t[i];
+}
+
+__global__ void contact_init_kernel(int* out) {
+    const int t = threadIdx.x;
+    if (t < 6) out[t] = t < 2 ? 0 : ((t & 1) ? INT_MIN : INT_MAX);
 }
 
 // bit i of nbmask[x] <=> x + e_i is an interior solid cell (bit 0: x itself).  Walls are not
@@ -505,6 +580,11 @@ cudaError_t launch_nbmask(const KParams& kp, int Q, const uint8_t* solid, uint32
 
 cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums, cudaStream_t st) {
     finish_sums_kernel<<<1, 256, 0, st>>>(partials, nblocks, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contact_init(int* out, cudaStream_t st) {
+    contact_init_kernel<<<1, 32, 0, st>>>(out);
     return cudaGetLastError();
 }
 

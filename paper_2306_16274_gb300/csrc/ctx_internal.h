@@ -21,9 +21,13 @@ struct lbm_ctx {
     unsigned* status = nullptr;  // device status word
     double* partials = nullptr;  // moments partial sums (4 per block)
     double* sums = nullptr;      // 4 doubles
-    float* staging = nullptr;    // ncell * max(Q, 4) floats for host transfers
+    float* staging = nullptr;    // host-transfer buffer, allocated on first use
+    size_t staging_floats = 0;
     uint8_t* solid_dev = nullptr;
     size_t bytes = 0;
+    // per 32 x 4 column and z plane: 1 if some cell there has a solid neighbour (mask only),
+    // computed on first use by a multi-domain batch, cleared when the fields are re-initialised
+    std::vector<uint8_t> tile_flags;
     long long partial_blocks = 0;
     // host state
     int parity = 0;              // 0: natural layout, 1: swapped (after an odd number of AA steps)

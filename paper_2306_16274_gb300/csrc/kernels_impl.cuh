@@ -62,6 +62,15 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const 
                                blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1);
 }
 
+// member population addressing of the multi-domain kernels
+#ifdef LBM_BATCH_ADDR64
+using BatchAddr = PlaneStride64;
+using BatchAddrStride = long long;
+#else
+using BatchAddr = PlaneIdx32;
+using BatchAddrStride = uint32_t;
+#endif
+
 // multi-domain density + psi pass: one block per tile of any member of the launch's table;
 // physics by value
 template <int PARITY, bool SOLIDS>
@@ -71,7 +80,7 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParam
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
-    const PlaneStride addr{m.base, m.plane};
+    const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
     psi_column<PARITY, SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x, t.y0 + threadIdx.y,
                                t.z0, min(t.z0 + t.zc, m.nz));
 }
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
-    const PlaneStride addr{m.base, m.plane};
+    const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
     collide_tile<PARITY, SOLIDS, MULTIPHASE>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc, ring);
 }
 
@@ -397,6 +406,51 @@ __global__ void gather_kernel(KParams kp, const float* __restrict__ f, const uin
     for (int i = 0; i < Q; ++i) out[i * kp.ncell + c.idx] = p[i];
 }
 
+// ---- contact detector (Sec. III E, Sec. IV B): liquid fluid cells (rho > thr) with a solid
+// lattice neighbour (mask or wall), and the liquid footprint in the layer z = 0 above a bottom
+// wall.  out[0] += such cells, out[1] += liquid cells of the floor layer, out[2..5] = min / max
+// of their x and y.  rho is formed as the moments kernel forms it.
+constexpr int CT_BX = 32, CT_BY = 8;
+template <int PARITY>
+__global__ void __launch_bounds__(CT_BX * CT_BY) contact_kernel(KParams kp, const float* __restrict__ f,
+                                                              const uint32_t* __restrict__ nbmask, float thr,
+                                                              int* __restrict__ out) {
+    const int x = blockIdx.x * CT_BX + threadIdx.x;
+    const int y = blockIdx.y * CT_BY + threadIdx.y;
+    const int z = blockIdx.z;
+    bool wet = false;
+    if (x < kp.nx && y < kp.ny) {
+        const Cell c = make_cell(kp, x, y, z);
+        const uint32_t bits = solid_bits<Q>(kp, nbmask, c);
+        if (!(bits & 1u) && bits != 0u) {
+            float p[Q], m[Q];
+            gather<Q, PARITY, true>(kp, f, c, bits, p);
+            to_moments<Q>(p, m);
+            wet = m[0] > thr;
+        }
+    }
+    const bool on_floor = wet && kp.wall_z && z == 0;
+    const int nwet = __syncthreads_count(wet);
+    const int nfloor = __syncthreads_count(on_floor);
+    if (nfloor) {
+        const unsigned lane_any = __ballot_sync(0xffffffffu, on_floor);
+        const int xmin = __reduce_min_sync(0xffffffffu, on_floor ? x : INT_MAX);
+        const int xmax = __reduce_max_sync(0xffffffffu, on_floor ? x : INT_MIN);
+        const int ymin = __reduce_min_sync(0xffffffffu, on_floor ? y : INT_MAX);
+        const int ymax = __reduce_max_sync(0xffffffffu, on_floor ? y : INT_MIN);
+        if (lane_any && (threadIdx.x & 31) == 0) {
+            atomicMin(out + 2, xmin);
+            atomicMax(out + 3, xmax);
+            atomicMin(out + 4, ymin);
+            atomicMax(out + 5, ymax);
+        }
+    }
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        if (nwet) atomicAdd(out, nwet);
+        if (nfloor) atomicAdd(out + 1, nfloor);
+    }
+}
+
 dim3 psi_grid(const KParams& kp) {
     return dim3((kp.nx + PSI_BX - 1) / PSI_BX, (kp.ny + PSI_BY - 1) / PSI_BY, kp.nz);
 }
@@ -499,6 +553,14 @@ cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams& phys, const BatchD
     else if (parity == 0) psi_batch_kernel<0, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
     else if (!solids) psi_batch_kernel<1, false><<<ntiles, b, 0, st>>>(phys, doms, tiles);
     else psi_batch_kernel<1, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, const float* f, const uint32_t* nbmask,
+                                             float thr, int* out, cudaStream_t st) {
+    const dim3 g((kp.nx + CT_BX - 1) / CT_BX, (kp.ny + CT_BY - 1) / CT_BY, kp.nz), b(CT_BX, CT_BY);
+    if (parity == 0) contact_kernel<0><<<g, b, 0, st>>>(kp, f, nbmask, thr, out);
+    else contact_kernel<1><<<g, b, 0, st>>>(kp, f, nbmask, thr, out);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 
 #include <stdint.h>
 
+#include <climits>
+
 #include "lbm_internal.h"
 #include "transform_q19.cuh"
 #include "transform_q27.cuh"
@@ -350,18 +352,30 @@ __device__ __forceinline__ uint32_t solid_bits32(const GM& g, const uint32_t* __
     return bits;
 }
 
-// Addressing of population plane i: per-plane base pointers from the kernel parameters
-// (constant bank, free operands) for single-domain launches ...
+// Address of cell offset `off` in population plane i: per-plane base pointers from the kernel
+// parameters (constant bank, free operands) for single-domain launches ...
 struct PlanePtrs {
     const KParams& kp;
-    __device__ __forceinline__ float* plane(int i) const { return kp.fq[i]; }
+    __device__ __forceinline__ float* ptr(int i, uint32_t off) const { return kp.fq[i] + off; }
 };
-// ... or one base pointer and the plane stride in registers for multi-domain launches, whose
-// parameters come from memory (27 pointer loads per access pattern would cost issue slots).
-struct PlaneStride {
-    float* base;
-    long long stride;
-    __device__ __forceinline__ float* plane(int i) const { return base + i * stride; }
+// ... or, for multi-domain launches, one base pointer and a 32-bit plane stride: the whole
+// index i * plane + off stays in 32 bits (a member's Q planes hold < 2^32 floats), so each access
+// costs one integer multiply-add and one wide address computation.
+struct PlaneIdx32 {
+    const float* base;
+    uint32_t plane;
+    __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
+        return const_cast<float*>(base) + (uint32_t)((uint32_t)i * plane + off);
+    }
+};
+
+// 64-bit variant of the same (tuning alternative, LBM_BATCH_ADDR64).
+struct PlaneStride64 {
+    const float* base;
+    long long plane;
+    __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
+        return const_cast<float*>(base) + (long long)i * plane + off;
+    }
 };
 
 template <int Q, int PARITY, bool SOLIDS, class A>
@@ -369,11 +383,11 @@ __device__ __forceinline__ void gather32(const A& a, const Off32& o, uint32_t bi
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            p[i] = __ldg(a.plane(i) + o.c);
+            p[i] = __ldg(a.ptr(i, o.c));
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
-            p[i] = __ldg(a.plane(i) + o.c);
+            p[i] = __ldg(a.ptr(i, o.c));
         } else {
-            p[i] = __ldg(a.plane(OPP(i)) + o.nb(-EX(i), -EY(i), -EZ(i)));
+            p[i] = __ldg(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
         }
     }
 }
@@ -383,11 +397,11 @@ __device__ __forceinline__ void store32(const A& a, const Off32& o, uint32_t bit
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            a.plane(OPP(i))[o.c] = p[i];
+            *a.ptr(OPP(i), o.c) = p[i];
         } else if (SOLIDS && ((bits >> i) & 1u)) {
-            a.plane(OPP(i))[o.c] = p[i];
+            *a.ptr(OPP(i), o.c) = p[i];
         } else {
-            a.plane(i)[o.nb(EX(i), EY(i), EZ(i))] = p[i];
+            *a.ptr(i, o.nb(EX(i), EY(i), EZ(i))) = p[i];
         }
     }
 }

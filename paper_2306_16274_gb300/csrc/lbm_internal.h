@@ -87,6 +87,8 @@ struct BatchTile {
     cudaError_t launch_psi_batch_q##Q(const KParams& phys, const BatchDomTable& tab,                 \
                                       const BatchTile* tiles, int ntiles, int parity, int solids,      \
                                       cudaStream_t st);                                               \
+    cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const float* f,                  \
+                                    const uint32_t* nbmask, float thr, int* out, cudaStream_t st);   \
     int tile_height_q##Q();                                                                         \
     int resident_blocks_q##Q();
 
@@ -96,6 +98,7 @@ LBM_DECLARE_LAUNCHERS(27)
 // Lattice-independent kernels (capi.cu)
 cudaError_t launch_nbmask(const KParams& kp, int Q, const uint8_t* solid, uint32_t* nbmask, cudaStream_t st);
 cudaError_t launch_finish_sums(const double* partials, int nblocks, double* sums, cudaStream_t st);
+cudaError_t launch_contact_init(int* out, cudaStream_t st);   // out[6] = 0, 0, INT_MAX, INT_MIN, INT_MAX, INT_MIN
 
 // Sets the message lbm_last_error(NULL) returns on this thread (context-free entry points).
 void set_thread_error(const char* msg);

@@ -68,6 +68,8 @@ def lib():
         "lbm_get_kernel_timing": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "lbm_step_count": (I64, [P]),
         "lbm_device_bytes": (ctypes.c_size_t, [P]),
+        "lbm_estimate_bytes": (I32, [ctypes.POINTER(lbm_params), I32, ctypes.POINTER(ctypes.c_size_t)]),
+        "lbm_contact": (I32, [P, ctypes.c_float, P, I32]),
         "lbm_destroy": (V, [P]),
         "lbm_last_error": (ctypes.c_char_p, [P]),
         "lbm_status_string": (ctypes.c_char_p, [I32]),
@@ -156,6 +158,21 @@ def field_totals_noalloc(rho, u, totals, stream=None):
                                     ctypes.c_void_p(_stream_handle(stream)))
     if st != 0:
         raise LBMError(st, L.lbm_last_error(None).decode())
+
+
+def estimate_bytes(params, with_solid=False):
+    """lbm_estimate_bytes: device bytes a Simulation of `params` holds once initialised from device
+    memory (with a solid mask if with_solid), computed without allocating."""
+    L = lib()
+    c = params.to_c()
+    out = ctypes.c_size_t()
+    st = L.lbm_estimate_bytes(ctypes.byref(c), 1 if with_solid else 0, ctypes.byref(out))
+    if st != 0:
+        raise LBMError(st, L.lbm_last_error(None).decode())
+    return int(out.value)
+
+
+CONTACT_FIELDS = ("wet", "floor", "xmin", "xmax", "ymin", "ymax")
 
 
 def _torch():
@@ -278,6 +295,20 @@ class Simulation:
         else:
             out = np.empty((self.Q, nz, ny, nx), dtype=np.float32)
             self._check(self._L.lbm_get_populations(self._ctx, out.ctypes.data, 0))
+        return out
+
+    def contact(self, rho_threshold, out=None):
+        """lbm_contact: liquid cells (rho > rho_threshold) touching solids and the liquid footprint on a
+        bottom wall.  With out=None the call synchronises and returns a dict over CONTACT_FIELDS; with
+        `out` an int32 CUDA tensor of 6 elements (e.g. a row of a larger buffer) it only enqueues."""
+        if out is None:
+            h = (ctypes.c_int32 * 6)()
+            self._check(self._L.lbm_contact(self._ctx, float(rho_threshold), h, 0))
+            return dict(zip(CONTACT_FIELDS, list(h)))
+        torch = _torch()
+        if out.dtype != torch.int32 or out.numel() != 6 or not out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous int32 CUDA tensor of 6 elements")
+        self._check(self._L.lbm_contact(self._ctx, float(rho_threshold), out.data_ptr(), 1))
         return out
 
     def set_populations(self, f):

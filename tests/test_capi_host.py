@@ -87,3 +87,32 @@ def test_per_lattice_launch_helpers_have_internal_linkage(lib):
     for r in rows:
         kind = r.split()[1] if len(r.split()) > 2 else r.split()[0]
         assert kind in ("t", "d", "b", "r"), r
+
+
+def test_extent_limit_is_enforced(lib):
+    c = L.Params(lattice=19, shape=(1, 1, 65536)).to_c()
+    ctx = ctypes.c_void_p()
+    assert lib.lbm_create(ctypes.byref(c), None, ctypes.byref(ctx)) == 1
+    assert b"LBM_MAX_EXTENT" in lib.lbm_last_error(None)
+
+
+def test_estimate_bytes_counts_the_resident_state(lib):
+    # populations in planes padded to 64 cells, psi, the 64-byte status word, the reduction
+    # scratch (4 doubles per 32 x 4 x 2 block plus 4 totals) and 5 bytes per cell for a mask
+    for Q, shape in ((19, (256, 256, 256)), (27, (37, 21, 18)), (19, (1, 1, 1))):
+        nx, ny, nz = shape
+        n = nx * ny * nz
+        plane = (n + 63) // 64 * 64
+        blocks = -(-nx // 32) * -(-ny // 4) * -(-nz // 2)
+        want = Q * plane * 4 + n * 4 + 64 + blocks * 32 + 32
+        p = L.Params(lattice=Q, shape=shape)
+        assert L.estimate_bytes(p) == want
+        assert L.estimate_bytes(p, with_solid=True) == want + 5 * n
+    with pytest.raises(L.LBMError) as e:
+        L.estimate_bytes(L.Params(lattice=21))
+    assert e.value.status == 1
+
+
+def test_contact_rejects_null_context(lib):
+    out = (ctypes.c_int32 * 6)()
+    assert lib.lbm_contact(None, ctypes.c_float(0.5), out, 0) == 1

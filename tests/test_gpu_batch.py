@@ -55,9 +55,9 @@ def test_batch_equals_members_stepped_alone(nsteps):
     b.step(nsteps)
     b.sync()
     info = b.info()
-    # groups: one per (lattice, solid handling, physics); the walled droplet without interior
-    # solids has its interior tiles in a plain group and its boundary tiles in a solid group
-    assert info["groups"] == 7
+    # groups: one per (lattice, solid handling, physics); a member with walls or solids has its
+    # solid-free tiles in a plain group and the others in a solid group
+    assert info["groups"] == 8
     if nsteps >= 2:
         assert info["graph_mode"] in (1, 2)
     for a, t in zip(alone, together):

@@ -14,6 +14,9 @@ Recipes (sizes and structure of the paper's cases):
   vapour, the "plain method at scale" workload).
 * ``impact``: a droplet above a flat wall moving toward it (Sec. III E / IV A).
 * ``cylinder_mask``: a solid cylinder lying on the bottom wall (Sec. IV B).
+* ``cylinder_impact``: a droplet falling onto such a cylinder (Sec. IV B), and
+  ``serving_jobs``: a seeded mix of cylinder-impact and static-droplet jobs of uneven sizes
+  with Poisson arrival times, the request stream of a job server.
 * ``shear_wave`` / ``taylor_green``: single-phase decaying flows.
 * ``perturbed``: a smooth random density / velocity field for one-step parity tests.
 """
@@ -194,3 +197,48 @@ def perturbed(shape, seed, rho0=1.0, drho=0.05, U=0.05, modes=3):
     rho = rho0 + field(drho)
     u = np.stack([field(U), field(U), field(U)])
     return rho, u
+
+
+def cylinder_impact(shape, R0, Rc, rho_l, rho_v, U, gap=3.0, W=2.0):
+    """Sec. IV B: a cylinder of radius Rc lying on the bottom wall along y (axis at height
+    Rc - 1/2), and above its crest a droplet of radius R0 whose surface is `gap` cells higher,
+    centred over the axis and moving with (0, 0, -U).  Returns (rho, u, solid); solid cells
+    carry rho = rho_v (ignored by both implementations)."""
+    nx, ny, nz = shape
+    solid = cylinder_mask(shape, Rc, axis="y")
+    zc = 2.0 * Rc - 0.5 + gap + R0
+    rho, u = droplet(shape, R0, rho_l, rho_v, W=W, center=(nx / 2.0 - 0.5, ny / 2.0, zc), periodic=False)
+    frac = np.clip((rho - rho_v) / (rho_l - rho_v), 0.0, 1.0)
+    u[2] = -U * frac
+    rho = np.where(solid == 1, rho_v, rho)
+    u[:, solid == 1] = 0.0
+    return rho, u, solid
+
+
+def serving_jobs(n_jobs, rate, seed=2306, edge=(64, 160), impact_fraction=0.5):
+    """A request stream: `n_jobs` jobs with Poisson arrivals of `rate` per second (exponential
+    gaps drawn from numpy seed `seed` + 1, so the jobs, drawn from `seed`, are the same at any
+    rate).  Each job is a dict: name, kind ("impact" or "droplet"), lattice
+    (19 or 27 by a fair coin), edge L ~ U{edge}, and for impacts the cylinder-to-droplet ratio
+    R/R0 ~ U[0.2, 2] with R0 = L / 6 (Sec. IV B), the domain height raised to fit cylinder and
+    droplet; for static droplets a radius ~ U[L/8, L/4] (a parameter sweep).  Only sizes and
+    draws: the physical parameters are chosen by the caller."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.random.default_rng(seed + 1)        # separate stream: same jobs at any rate
+    t = 0.0
+    jobs = []
+    for k in range(n_jobs):
+        t += float(arrivals.exponential(1.0 / rate)) if rate > 0 else 0.0
+        L = int(rng.integers(edge[0], edge[1] + 1))
+        Q = 19 if rng.random() < 0.5 else 27
+        if rng.random() < impact_fraction:
+            R0 = L / 6.0
+            ratio = float(rng.uniform(0.2, 2.0))
+            Rc = ratio * R0
+            nz = max(int(round(5 * R0)), int(np.ceil(2 * Rc + 2 * R0 + 3 + R0)))
+            jobs.append(dict(name=f"impact{k}", kind="impact", lattice=Q, shape=(L, L, nz), R0=R0, Rc=Rc,
+                             arrival=t))
+        else:
+            R = float(rng.uniform(L / 8.0, L / 4.0))
+            jobs.append(dict(name=f"droplet{k}", kind="droplet", lattice=Q, shape=(L, L, L), R=R, arrival=t))
+    return jobs

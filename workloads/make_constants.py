@@ -2,7 +2,8 @@
 
 Stores the Carnahan-Starling critical point and the Maxwell coexistence densities
 at T = 0.7 T_c and T = 0.5 T_c for a = 0.5, b = 4, R = 1 (the static-droplet and
-at-scale workloads), and the piecewise-EOS spinodal densities of Eq. e20 for
+at-scale workloads), the surface tension at 0.7 T_c for kappa = 0 and 0.3 (Laplace's law,
+used to set impact velocities and capillary times), and the piecewise-EOS spinodal densities of Eq. e20 for
 rho_v = 0.001, rho_l = 1 with the slopes of Eq. e21.  Run from the repository root:
 
     python -m workloads.make_constants
@@ -35,6 +36,24 @@ def planar_equilibrium(cs, steps=10000):
             "setup": "D3Q19 slab 160x1x1, sigma=0.1, kappa=0.5, s2b=1.0"}
 
 
+def column_surface_tension(cs, kappa, steps=1000):
+    """Surface tension of the C-S fluid at T = 0.7 T_c (D3Q19, G = -1, sigma = 0.1, default
+    rates) from Laplace's law on a liquid column (Sec. III C): gamma = (p_in - p_out) R, the mean
+    over R = 8 and R = 12 in a 48 x 48 x 1 periodic box after `steps` steps, pressures from the
+    EOS at the column centre and the far corner."""
+    t = cs["T0.7"]
+    vals = []
+    for R in (8, 12):
+        p = lbm.Params(lattice=19, shape=(48, 48, 1), eos="cs", eos_p=(cs["a"], cs["b"], cs["R"], t["T"]), G=-1.0,
+                       sigma=0.1, kappa=kappa)
+        s = lbm.State.from_fields(p, *workloads.cylinder_droplet((48, 48, 1), R, t["rho_l"], t["rho_v"])).run(steps)
+        r = s.moments()[0][0]
+        pin = eos.cs_pressure(r[24, 24], cs["a"], cs["b"], cs["R"], t["T"])
+        pout = eos.cs_pressure(r[0, 0], cs["a"], cs["b"], cs["R"], t["T"])
+        vals.append((pin - pout) * R)
+    return float(np.mean(vals))
+
+
 def main():
     warnings.simplefilter("ignore")
     a, b, R = 0.5, 4.0, 1.0
@@ -49,6 +68,8 @@ def main():
     out["piecewise"] = {"rho_v": 0.001, "rho_l": 1.0, "rho1": r1, "rho2": r2,
                         "theta_v": tv, "theta_m": tm, "theta_l": tl}
     out["cs"]["planar_T0.5"] = planar_equilibrium(out["cs"])
+    out["cs"]["gamma_T0.7"] = {f"kappa{k}": column_surface_tension(out["cs"], k) for k in (0.0, 0.3)}
+    out["cs"]["gamma_T0.7"]["setup"] = "Laplace column 48x48x1, R = 8 and 12, 1000 steps, D3Q19, sigma = 0.1"
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "constants.json")
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1, sort_keys=True)
