@@ -129,7 +129,9 @@ lbm_status lbm_init_fields(lbm_ctx* ctx, const float* rho, const float* u, const
                            int ptrs_on_device);
 
 /* Enqueues n >= 0 time steps on the context's stream and returns without
- * waiting.  Returns a sticky error recorded by an earlier lbm_sync. */
+ * waiting.  Returns a sticky error recorded by an earlier lbm_sync.  A domain
+ * with walls or solids is stepped through the tile path of the batches below
+ * (same results, solid-free tiles skip the solid tests). */
 lbm_status lbm_step(lbm_ctx* ctx, int32_t n);
 
 /* Waits for the context's stream and reads the device status word:
@@ -205,19 +207,26 @@ void lbm_destroy(lbm_ctx* ctx);
 
 /* ---------------------------------------------------------------- batches
  * Many independent domains advanced together (the paper's method applied to a set
- * of jobs; the paper itself runs one domain at a time).  Members are grouped by
- * (lattice, walls or solids present, multiphase); each time step costs one
- * collide-stream launch and one density/psi launch per group, whose blocks are
- * tiles of every member of the group.  Per cell the arithmetic is the
- * single-domain kernels', so every member evolves bitwise as if stepped alone.
- * Runs of steps are replayed from one CUDA graph (a device-side loop), so n steps
- * cost one graph launch.
+ * of jobs; the paper itself runs one domain at a time).  Every member is cut into
+ * tiles of 32 x 4 columns and runs of z planes; a tile whose cells have no solid
+ * neighbour (mask or wall) goes to a group without solid handling.  Groups are
+ * keyed by (lattice, solid handling, physical parameters); each time step costs,
+ * per group and per 64 members, one collide-stream launch and one density/psi
+ * launch whose blocks are tiles of all those members, and the groups of one pass
+ * run concurrently.  Per cell the arithmetic is the single-domain kernels', so
+ * every member evolves bitwise as if stepped alone.  Runs of steps are replayed
+ * from one CUDA graph (a device-side loop), so n steps cost one graph launch.
+ * lbm_step itself takes this path (a batch of one) for a domain with walls or
+ * solids, unless kernel timing is on.
  *
  * lbm_batch_create: ctxs are n >= 1 distinct, initialised contexts on the current
- *   device that have taken the same number of steps modulo 2; the batch keeps the
+ *   device that have taken the same number of steps modulo 2, each holding fewer
+ *   than 2^32 population values (Q x cells rounded up to 64); the batch keeps the
  *   pointers (the caller keeps ownership and must not destroy a member while the
- *   batch exists, nor re-initialise a member with a different solid set-up).  Work
- *   is enqueued on cuda_stream; the caller orders it with the members' streams.
+ *   batch exists).  A member re-initialised with another solid mask is re-tiled
+ *   at the next lbm_batch_step.  Work is enqueued on cuda_stream; the caller
+ *   orders it with the members' streams.  A member's own zchunk, if set, is used
+ *   until lbm_batch_tune chooses one.
  *   Errors: LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA (message in
  *   lbm_last_error(NULL)).
  * lbm_batch_step: enqueues n >= 0 steps of every member (does not wait) and
@@ -227,7 +236,7 @@ void lbm_destroy(lbm_ctx* ctx);
  *   with each candidate z-chunk (automatic, 1, 2, 4, 8, 16, 32 planes per block),
  *   keeps the fastest per group and writes it to zchunk_out[g] for g < max_groups
  *   (0 = automatic).  The members advance by 7 x (trial_steps + 1) steps.
- * lbm_batch_info: number of groups, tiles of the collide launches, graph mode
+ * lbm_batch_info: number of groups, tiles of all launches of one pass, graph mode
  *   (0 not recorded yet, 1 device-side WHILE loop, 2 replayed two-step graph). */
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, lbm_batch** out);

@@ -205,7 +205,8 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
         lbm_status fs = member_tile_flags(b, c, th);
         if (fs != LBM_OK) return fs;
         int zc;
-        if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);
+        if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);            // the batch's tuned choice
+        else if (k.zchunk > 0) zc = std::min(k.zchunk, k.nz);       // the member's own setting
         else {
             const long long ch = std::min<long long>(chunks_auto, k.nz);
             zc = std::min(ZC_AUTO_MAX, (int)((k.nz + ch - 1) / ch));

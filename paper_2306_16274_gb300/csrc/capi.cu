@@ -343,6 +343,17 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
     if (c->sticky != LBM_OK) return c->sticky;
+    if (has_solids(c) && !c->timing && n > 0 && (unsigned long long)c->Q * (unsigned long long)c->kp.plane <= 0xFFFFFFFFull) {
+        // walls or solids: the tile path, which runs solid-free tiles without solid handling
+        if (!c->self_batch) {
+            lbm_ctx* self[1] = {c};
+            lbm_status bs = lbm_batch_create(self, 1, c->stream, &c->self_batch);
+            if (bs != LBM_OK) return fail(c, bs, std::string("tile path: ") + lbm_last_error(nullptr));
+        }
+        lbm_status bs = lbm_batch_step(c->self_batch, n);
+        if (bs != LBM_OK) return fail(c, bs, std::string("tile path: ") + lbm_batch_last_error(c->self_batch));
+        return LBM_OK;
+    }
     for (int32_t k = 0; k < n; ++k) {
         // psi of the current state is valid on entry: collide-stream, then density/psi of the new state
         if (c->timing) CK(c, record(c));
@@ -422,6 +433,10 @@ lbm_status lbm_set_populations(lbm_ctx* c, const float* f, int on_device) {
 
 lbm_status lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
     if (!c) return LBM_ERR_ARG;
+    if (c->self_batch) {   // bound to the old stream
+        lbm_batch_destroy(c->self_batch);
+        c->self_batch = nullptr;
+    }
     c->stream = (cudaStream_t)cuda_stream;
     return LBM_OK;
 }
@@ -479,6 +494,7 @@ lbm_status lbm_contact(lbm_ctx* c, float rho_threshold, int32_t* out, int on_dev
 
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
+    if (c->self_batch) lbm_batch_destroy(c->self_batch);
     if (c->stream || c->f) (void)cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) (void)cudaEventDestroy(e);
     void* ptrs[] = {c->f, c->psi, c->nbmask, c->status, c->partials, c->sums, c->staging, c->solid_dev};

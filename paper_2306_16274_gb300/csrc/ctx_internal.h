@@ -28,6 +28,9 @@ struct lbm_ctx {
     // per 32 x 4 column and z plane: 1 if some cell there has a solid neighbour (mask only),
     // computed on first use by a multi-domain batch, cleared when the fields are re-initialised
     std::vector<uint8_t> tile_flags;
+    // domains with walls or solids step through a one-member batch (created on first use): its
+    // tiles away from solids take the kernels without solid handling
+    lbm_batch* self_batch = nullptr;
     long long partial_blocks = 0;
     // host state
     int parity = 0;              // 0: natural layout, 1: swapped (after an odd number of AA steps)

@@ -154,3 +154,20 @@ def test_batch_groups_share_physics_and_regroup_on_new_mask():
     for a, t in zip(alone, together):
         assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
     b.close()
+
+
+@pytest.mark.parametrize("which", [2, 3])
+def test_single_domain_tile_path_equals_grid_path(which):
+    # a domain with walls or solids steps through its own one-member batch (solid-free tiles
+    # without solid handling); with kernel timing on it takes the whole-grid kernels instead.
+    # Both must give the same bits.
+    d, rho, u, solid = _members()[which]
+    tiles = U.run_gpu(d, rho, u, solid)
+    grid = U.run_gpu(d, rho, u, solid)
+    grid.set_kernel_timing(True)
+    for n in (7, 40):
+        tiles.step(n)
+        grid.step(n)
+        assert np.array_equal(tiles.populations().cpu().numpy(), grid.populations().cpu().numpy())
+    ms, launches = grid.kernel_timing()
+    assert launches["collide"] == 47 and launches["psi"] == 47
