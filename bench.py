@@ -40,10 +40,14 @@ WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves th
             "sigma=0.1, G=-1, the paper's default rates, FP32 populations (AA in place)")
 
 
-def algorithmic_bytes(Q):
+def algorithmic_bytes(Q, store="fp32"):
     """Bytes per cell update that the method must move: collide-stream reads and writes the Q
     populations and reads psi once (8Q + 4); the density/psi pass reads the Q populations and
-    writes psi (4Q + 4)."""
+    writes psi (4Q + 4).  Shifted FP16 store: 2-byte slots, and the density field the slots are
+    relative to is read by both passes and written by the density pass (collide 4Q + 12,
+    density/psi 2Q + 12)."""
+    if store == "fp16":
+        return {"collide": 4 * Q + 12, "psi": 2 * Q + 12, "step": 6 * Q + 24}
     return {"collide": 8 * Q + 4, "psi": 4 * Q + 4, "step": 12 * Q + 8}
 
 
@@ -169,11 +173,11 @@ def whole_job_mlups(world_size, cells, steps, ms_max):
 
 
 # ---------------------------------------------------------------- our arm
-def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None):
+def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None, store="fp32"):
     import torch
 
     from paper_2306_16274_gb300 import Params, Simulation
-    p = Params(lattice=Q, shape=SHAPE, **wparams)
+    p = Params(lattice=Q, shape=SHAPE, store=store, **wparams)
     stream = torch.cuda.Stream()
     sim = Simulation(p, stream=stream)
     with torch.cuda.stream(stream):
@@ -503,6 +507,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24)
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
@@ -536,6 +541,8 @@ def main():
     value = whole_job_mlups(ws, n, args.steps, ms)
     r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
     e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
+    f16 = {} if args.no_fp16 else {Q: run_lattice(Q, rho, u, wparams, args.steps, args.warmup, dist, store="fp16")
+                                   for Q in ((19,) if args.no_q27 else (19, 27))}
     batched = None if (args.no_batched or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
     serving = None if (args.no_serving or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
     if rank != 0:
@@ -575,6 +582,20 @@ def main():
                          "collide_gbs": ab27["collide"] * n / (c27 * 1e-3) / 1e9, "mass_drift_rel": r27["mass_drift"]}
     if e2e:
         line["e2e"] = e2e
+    if f16:
+        line["fp16_store"] = {"note": "shifted FP16 population store (FP32 arithmetic); accuracy against the FP64 "
+                                      "oracle is checked per result by tests/test_gpu_fp16.py"}
+        for Q, r in f16.items():
+            abh = algorithmic_bytes(Q, "fp16")
+            cms = r["kernel_ms"]["collide"] / max(r["kernel_launches"]["collide"], 1)
+            pms = r["kernel_ms"]["psi"] / max(r["kernel_launches"]["psi"], 1)
+            line["fp16_store"][f"d3q{Q}"] = {
+                "value": r["mlups_local"], "unit": UNIT, "ms_per_step": r["ms"] / args.steps,
+                "bytes_per_cell": abh["step"],
+                "hbm_frac_step": abh["step"] * n * args.steps / (r["ms"] * 1e-3) / 1e9 / peak,
+                "collide_gbs": abh["collide"] * n / (cms * 1e-3) / 1e9,
+                "psi_gbs": abh["psi"] * n / (pms * 1e-3) / 1e9, "mass_drift_rel": r["mass_drift"],
+                "device_bytes": r["device_bytes"]}
     if batched:
         line["batched"] = batched
     if serving:

@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 /* Largest nx, ny or nz: the density/psi pass launches one block row per z plane. */
 #define LBM_MAX_EXTENT 65535
@@ -73,6 +73,14 @@ enum {
     LBM_EOS_CS = 1,         /* Carnahan-Starling: eos_p = {a, b, R, T}                     */
     LBM_EOS_PIECEWISE = 2   /* piecewise linear, Eq. e19: eos_p = {rho1, rho2, theta_v,   */
                             /*   theta_m, theta_l}                                        */
+};
+
+/* population storage */
+enum {
+    LBM_STORE_FP32 = 0,     /* FP32 populations                                           */
+    LBM_STORE_FP16 = 1      /* shifted FP16: a slot holds f_i / rho_w - omega_i in half   */
+                            /* precision, rho_w the density of the cell that wrote it     */
+                            /* (kept in FP32, two fields of 4 bytes per cell); FP32 maths */
 };
 
 /* per-axis boundary */
@@ -103,6 +111,11 @@ typedef struct {
                             /* b * rho_c = 0.52177 (critical density); +inf: never           */
     int32_t zchunk;         /* tuning: z planes one collide block marches through; 0 = chosen */
                             /* from the domain size (results do not depend on it)            */
+    int32_t store;          /* LBM_STORE_FP32 (default) or LBM_STORE_FP16.  The paper stores */
+                            /* populations in full precision; FP16 halves their bytes and    */
+                            /* its error against the FP64 oracle is reported per result.     */
+                            /* FP16 contexts step with the whole-grid kernels and cannot     */
+                            /* join a batch.                                                 */
 } lbm_params;
 
 /* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,

@@ -433,6 +433,8 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, 
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return bfail(nullptr, LBM_ERR_ARG, "NULL context in the batch");
         if (!ctxs[i]->initialised) return bfail(nullptr, LBM_ERR_STATE, "every context must be initialised");
+        if (ctxs[i]->f16)
+            return bfail(nullptr, LBM_ERR_ARG, "contexts with the FP16 store cannot join a batch");
         if (ctxs[i]->parity != ctxs[0]->parity)
             return bfail(nullptr, LBM_ERR_STATE, "all contexts must have taken an equal number of steps mod 2");
         for (int j = 0; j < i; ++j)

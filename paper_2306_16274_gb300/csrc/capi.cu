@@ -64,6 +64,10 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         }
     }
     if (p->zchunk < 0) { why = "zchunk must be >= 0"; return LBM_ERR_ARG; }
+    if (p->store != LBM_STORE_FP32 && p->store != LBM_STORE_FP16) {
+        why = "store must be LBM_STORE_FP32 or LBM_STORE_FP16";
+        return LBM_ERR_ARG;
+    }
     if (p->variable_nu) {
         if (!(p->rho_l != p->rho_v) || !(p->nu_l > 0.0) || !(p->nu_v > 0.0)) {
             why = "variable viscosity needs rho_l != rho_v and nu_l, nu_v > 0";
@@ -140,17 +144,35 @@ bool has_solids(const lbm_ctx* c) {
     return c->nbmask != nullptr || c->kp.wall_x || c->kp.wall_y || c->kp.wall_z;
 }
 
+// The context's buffers as the launchers take them.  Shifted FP16 store: rbuf[rs] holds the
+// densities the stored slots were written with, rbuf[rs ^ 1] the newest densities.
+lbm::Bufs bufs(const lbm_ctx* c) {
+    lbm::Bufs b;
+    b.f = c->f;
+    b.psi = c->psi;
+    b.nbmask = c->nbmask;
+    b.status = c->status;
+    b.f16 = c->f16;
+    b.rsrc = c->f16 ? c->rbuf[c->rs] : nullptr;
+    b.rnew = c->f16 ? c->rbuf[c->rs ^ 1] : nullptr;
+    return b;
+}
+
+// density (+ psi) pass; with the FP16 store it also writes the densities the next collide pass
+// normalises with, so it runs for single-phase domains too
 cudaError_t run_psi(lbm_ctx* c) {
-    if (!c->kp.multiphase) return cudaSuccess;
+    if (!c->kp.multiphase && !c->f16) return cudaSuccess;
     const int s = has_solids(c);
-    return c->Q == 19 ? lbm::launch_psi_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream)
-                      : lbm::launch_psi_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream);
+    return c->Q == 19 ? lbm::launch_psi_q19(c->kp, c->parity, s, bufs(c), c->stream)
+                      : lbm::launch_psi_q27(c->kp, c->parity, s, bufs(c), c->stream);
 }
 
 cudaError_t run_collide(lbm_ctx* c) {
     const int s = has_solids(c);
-    return c->Q == 19 ? lbm::launch_collide_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream)
-                      : lbm::launch_collide_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, c->status, c->stream);
+    cudaError_t e = c->Q == 19 ? lbm::launch_collide_q19(c->kp, c->parity, s, bufs(c), c->stream)
+                               : lbm::launch_collide_q27(c->kp, c->parity, s, bufs(c), c->stream);
+    if (c->f16) c->rs ^= 1;   // the slots are now relative to the densities the collide pass used
+    return e;
 }
 
 cudaError_t record(lbm_ctx* c) {
@@ -176,7 +198,7 @@ cudaError_t drain_timing(lbm_ctx* c) {
         c->ms[1] += a;   // collide runs first in a step
         c->ms[0] += b;
         c->launches[1] += 1;
-        if (c->kp.multiphase) c->launches[0] += 1;
+        if (c->kp.multiphase || c->f16) c->launches[0] += 1;
     }
     c->ev_used = 0;
     return cudaSuccess;
@@ -222,9 +244,10 @@ cudaError_t ensure_staging(lbm_ctx* c, size_t floats) {
 }
 
 // Device bytes a context holds once initialised (host staging excluded).
-size_t resident_bytes(const KParams& k, int Q, bool with_solid) {
+size_t resident_bytes(const KParams& k, int Q, bool f16, bool with_solid) {
     const size_t n = (size_t)k.ncell;
-    size_t b = (size_t)Q * (size_t)k.plane * sizeof(float);   // populations
+    size_t b = (size_t)Q * (size_t)k.plane * (f16 ? 2 : sizeof(float));   // populations
+    if (f16) b += 2 * n * sizeof(float);                                   // two density fields
     b += n * sizeof(float);                                   // psi
     b += 64;                                                  // status word
     b += (size_t)lbm::moments_partial_blocks(k) * 4 * sizeof(double) + 4 * sizeof(double);
@@ -274,9 +297,13 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         return e;
     };
     cudaError_t e = cudaGetDevice(&c->device);
-    if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * sizeof(float));
+    c->f16 = params->store == LBM_STORE_FP16;
+    const size_t esize = c->f16 ? 2 : sizeof(float);   // FP16 slots are __half
+    if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * esize);
     if (e == cudaSuccess)
-        for (int i = 0; i < c->Q; ++i) c->kp.fq[i] = c->f + (size_t)i * plane;
+        for (int i = 0; i < c->Q; ++i)
+            c->kp.fq[i] = reinterpret_cast<float*>(reinterpret_cast<char*>(c->f) + (size_t)i * plane * esize);
+    for (int k = 0; k < 2 && c->f16 && e == cudaSuccess; ++k) e = alloc((void**)&c->rbuf[k], (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
@@ -326,8 +353,8 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->nbmask = nullptr;
     }
     c->tile_flags.clear();
-    CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream)
-                     : lbm::launch_init_q27(c->kp, c->f, d_rho, d_u, c->nbmask, c->stream));
+    CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, bufs(c), d_rho, d_u, c->stream)
+                     : lbm::launch_init_q27(c->kp, bufs(c), d_rho, d_u, c->stream));
     c->parity = 0;
     c->t = 0;
     c->sticky = LBM_OK;
@@ -343,7 +370,8 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
     if (c->sticky != LBM_OK) return c->sticky;
-    if (has_solids(c) && !c->timing && n > 0 && (unsigned long long)c->Q * (unsigned long long)c->kp.plane <= 0xFFFFFFFFull) {
+    if (has_solids(c) && !c->timing && !c->f16 && n > 0 &&
+        (unsigned long long)c->Q * (unsigned long long)c->kp.plane <= 0xFFFFFFFFull) {
         // walls or solids: the tile path, which runs solid-free tiles without solid handling
         if (!c->self_batch) {
             lbm_ctx* self[1] = {c};
@@ -381,10 +409,8 @@ lbm_status lbm_get_moments(lbm_ctx* c, float* rho, float* u, double* sums, int o
     float* d_u = on_device ? u : (u ? c->staging + n : nullptr);
     int nb = 0;
     const int s = has_solids(c);
-    CK(c, c->Q == 19 ? lbm::launch_moments_q19(c->kp, c->parity, s, c->f, c->psi, c->nbmask, d_rho, d_u, c->partials,
-                                               &nb, c->stream)
-                     : lbm::launch_moments_q27(c->kp, c->parity, s, c->f, c->psi, c->nbmask, d_rho, d_u, c->partials,
-                                               &nb, c->stream));
+    CK(c, c->Q == 19 ? lbm::launch_moments_q19(c->kp, c->parity, s, bufs(c), d_rho, d_u, c->partials, &nb, c->stream)
+                     : lbm::launch_moments_q27(c->kp, c->parity, s, bufs(c), d_rho, d_u, c->partials, &nb, c->stream));
     CK(c, lbm::launch_finish_sums(c->partials, nb, c->sums, c->stream));
     if (!on_device) {
         if (rho) CK(c, cudaMemcpyAsync(rho, d_rho, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -410,8 +436,8 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int on_device) {
     if (!on_device) CK(c, ensure_staging(c, (size_t)c->Q * n));
     float* dst = on_device ? f : c->staging;
     const int s = has_solids(c);
-    CK(c, c->Q == 19 ? lbm::launch_gather_q19(c->kp, c->parity, s, c->f, c->nbmask, dst, c->stream)
-                     : lbm::launch_gather_q27(c->kp, c->parity, s, c->f, c->nbmask, dst, c->stream));
+    CK(c, c->Q == 19 ? lbm::launch_gather_q19(c->kp, c->parity, s, bufs(c), dst, c->stream)
+                     : lbm::launch_gather_q27(c->kp, c->parity, s, bufs(c), dst, c->stream));
     if (!on_device) CK(c, cudaMemcpyAsync(f, dst, (size_t)c->Q * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -420,8 +446,21 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int on_device) {
 lbm_status lbm_set_populations(lbm_ctx* c, const float* f, int on_device) {
     if (!c || !f) return LBM_ERR_ARG;
     const long long n = c->kp.ncell;
-    CK(c, cudaMemcpy2DAsync(c->f, c->kp.plane * sizeof(float), f, n * sizeof(float), n * sizeof(float), c->Q,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->f16) {
+        // densities of the given state, then the slots relative to them
+        const float* d_f = f;
+        if (!on_device) {
+            CK(c, ensure_staging(c, (size_t)c->Q * n));
+            CK(c, cudaMemcpyAsync(c->staging, f, (size_t)c->Q * n * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream));
+            d_f = c->staging;
+        }
+        CK(c, c->Q == 19 ? lbm::launch_f16_restore_q19(c->kp, bufs(c), d_f, c->stream)
+                         : lbm::launch_f16_restore_q27(c->kp, bufs(c), d_f, c->stream));
+    } else {
+        CK(c, cudaMemcpy2DAsync(c->f, c->kp.plane * sizeof(float), f, n * sizeof(float), n * sizeof(float), c->Q,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    }
     c->parity = 0;
     c->sticky = LBM_OK;
     CK(c, cudaMemsetAsync(c->status, 0, 64, c->stream));
@@ -470,7 +509,7 @@ lbm_status lbm_estimate_bytes(const lbm_params* params, int32_t with_solid, size
     if (v != LBM_OK) return fail(nullptr, v, why);
     const long long n = (long long)params->nx * params->ny * params->nz;
     const KParams k = derive(*params, (n + 63) / 64 * 64);
-    *bytes = resident_bytes(k, params->lattice, with_solid != 0);
+    *bytes = resident_bytes(k, params->lattice, params->store == LBM_STORE_FP16, with_solid != 0);
     return LBM_OK;
 }
 
@@ -481,9 +520,8 @@ lbm_status lbm_contact(lbm_ctx* c, float rho_threshold, int32_t* out, int on_dev
     int* d_out = on_device ? reinterpret_cast<int*>(out) : reinterpret_cast<int*>(c->sums);   // sums: 32 bytes
     CK(c, lbm::launch_contact_init(d_out, c->stream));
     if (has_solids(c))
-        CK(c, c->Q == 19 ? lbm::launch_contact_q19(c->kp, c->parity, c->f, c->nbmask, rho_threshold, d_out, c->stream)
-                         : lbm::launch_contact_q27(c->kp, c->parity, c->f, c->nbmask, rho_threshold, d_out,
-                                                   c->stream));
+        CK(c, c->Q == 19 ? lbm::launch_contact_q19(c->kp, c->parity, bufs(c), rho_threshold, d_out, c->stream)
+                         : lbm::launch_contact_q27(c->kp, c->parity, bufs(c), rho_threshold, d_out, c->stream));
     if (on_device) return LBM_OK;
     int32_t h[6];
     CK(c, cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -497,7 +535,8 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->self_batch) lbm_batch_destroy(c->self_batch);
     if (c->stream || c->f) (void)cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) (void)cudaEventDestroy(e);
-    void* ptrs[] = {c->f, c->psi, c->nbmask, c->status, c->partials, c->sums, c->staging, c->solid_dev};
+    void* ptrs[] = {c->f, c->psi, c->nbmask, c->status, c->partials, c->sums, c->staging, c->solid_dev,
+                    c->rbuf[0], c->rbuf[1]};
     for (void* p : ptrs)
         if (p) (void)cudaFree(p);
     delete c;

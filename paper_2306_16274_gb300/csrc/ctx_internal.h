@@ -15,7 +15,10 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     // device state
-    float* f = nullptr;          // Q planes of `plane` floats (AA layout)
+    float* f = nullptr;          // Q planes of `plane` slots (AA layout): floats, or __half with f16
+    int f16 = 0;                 // shifted FP16 store (LBM_STORE_FP16)
+    float* rbuf[2] = {nullptr, nullptr};   // f16: density fields, see bufs() in capi.cu
+    int rs = 0;
     float* psi = nullptr;        // ncell floats
     uint32_t* nbmask = nullptr;  // ncell words, only when a solid mask was given
     unsigned* status = nullptr;  // device status word

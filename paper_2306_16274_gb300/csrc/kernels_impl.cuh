@@ -1,6 +1,8 @@
 // Kernels of one lattice; included by kernels_q19.cu / kernels_q27.cu with LBM_Q set.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_device.cuh"
 
 #ifndef LBM_Q
@@ -16,11 +18,12 @@ constexpr int Q = LBM_Q;
 constexpr int PSI_BX = 32, PSI_BY = 4;
 
 // cells (x, y, z) for z in [z0, z1) of one column: pull the populations (AA phase PARITY),
-// rho = sum f, psi from the equation of state
-template <int PARITY, bool SOLIDS, class GM, class A>
+// rho = sum f, psi from the equation of state.  F16: the slots hold the shifted FP16 store,
+// read with the densities rsrc they were written with; the new densities go to rdst.
+template <int PARITY, bool SOLIDS, bool F16, class GM, class A>
 __device__ __forceinline__ void psi_column(const KParams& kp, const GM& g, const A& addr, float* __restrict__ psi,
                                            const uint32_t* __restrict__ nbmask, unsigned* status, int x, int y,
-                                           int z0, int z1) {
+                                           int z0, int z1, const float* __restrict__ rsrc, float* __restrict__ rdst) {
     const int nx = g.nx(), ny = g.ny(), nz = g.nz();
     if (x >= nx || y >= ny) return;
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
@@ -38,28 +41,30 @@ __device__ __forceinline__ void psi_column(const KParams& kp, const GM& g, const
         o.c = o.zo[1] + o.yo[1] + o.xo[1];
         const uint32_t bits = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z) : 0u;
         if (bits & 1u) {
-            psi[o.c] = 0.0f;
+            if (kp.multiphase) psi[o.c] = 0.0f;
+            if (F16) rdst[o.c] = 1.0f;
             continue;
         }
         float p[Q];
         gather32<Q, PARITY, SOLIDS>(addr, o, bits, p);
+        if (F16) denorm<Q, SOLIDS>(p, bits, RsOff32{rsrc, o});
         float rho = 0.0f;
 #pragma unroll
         for (int i = 0; i < Q; ++i) rho += p[i];
-        psi[o.c] = eval_psi(kp, rho, status);
+        if (F16) rdst[o.c] = rho;
+        if (kp.multiphase) psi[o.c] = eval_psi(kp, rho, status);
     }
 }
 
-template <int PARITY, bool SOLIDS>
-__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, const float* __restrict__ f,
-                                                            float* __restrict__ psi,
-                                                            const uint32_t* __restrict__ nbmask,
-                                                            unsigned* status) {
-    (void)f;   // addressed through kp.fq
+template <int PARITY, bool SOLIDS, bool F16>
+__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, float* __restrict__ psi,
+                                                            const uint32_t* __restrict__ nbmask, unsigned* status,
+                                                            const float* __restrict__ rsrc,
+                                                            float* __restrict__ rdst) {
     const KGeom g{kp};
-    const PlanePtrs addr{kp};
-    psi_column<PARITY, SOLIDS>(kp, g, addr, psi, nbmask, status, blockIdx.x * PSI_BX + threadIdx.x,
-                               blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1);
+    const PlanePtrsT<typename std::conditional<F16, __half, float>::type> addr{kp};
+    psi_column<PARITY, SOLIDS, F16>(kp, g, addr, psi, nbmask, status, blockIdx.x * PSI_BX + threadIdx.x,
+                                    blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1, rsrc, rdst);
 }
 
 // member population addressing of the multi-domain kernels
@@ -81,8 +86,8 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParam
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
-    psi_column<PARITY, SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x, t.y0 + threadIdx.y,
-                               t.z0, min(t.z0 + t.zc, m.nz));
+    psi_column<PARITY, SOLIDS, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x,
+                                      t.y0 + threadIdx.y, t.z0, min(t.z0 + t.zc, m.nz), nullptr, nullptr);
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
@@ -137,11 +142,14 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 #endif
 
 // One tile: cells [x0, x0+32) x [y0, y0+ZM_BY) marching through planes [z0, z0+zchunk); `addr`
-// locates population planes (PlanePtrs or PlaneStride).
-template <int PARITY, bool SOLIDS, bool MULTIPHASE, class GM, class A>
+// locates population planes.  F16 (shifted FP16 store): the densities the slots were written
+// with (rsrc) follow the march in a second shared ring `rring`; outputs are written relative
+// to the cell's current density rown.
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, class GM, class A>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
-                                             int z0, int zchunk, float (*ring)[ZM_RP]) {
+                                             int z0, int zchunk, float (*ring)[ZM_RP], float (*rring)[ZM_RP],
+                                             const float* __restrict__ rsrc, const float* __restrict__ rown) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x = x0 + tx, y = y0 + ty;
     const int nx = g.nx(), ny = g.ny(), nz = g.nz();
@@ -175,6 +183,10 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         load_psi_plane(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
         load_psi_plane(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
     }
+    if (F16) {
+        load_psi_plane(rring[0], rsrc, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane(rring[1], rsrc, z0, nz, g.wall_z(), nxy, goff, gok, tid);
+    }
 #if LBM_ZM_PREFETCH
     // populations of the first plane, then of plane z+1 while plane z is computed
     float pn[Q];
@@ -187,10 +199,9 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
 #endif
     const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
     for (int z = z0, j = 0; z < zend; ++z, ++j) {
-        if (MULTIPHASE) {
-            load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
-            __syncthreads();
-        }
+        if (MULTIPHASE) load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        if (F16) load_psi_plane(rring[(j + 2) & 3], rsrc, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        if (MULTIPHASE || F16) __syncthreads();
         if (!act_xy) continue;
 #if LBM_ZM_PREFETCH
         float p[Q];
@@ -211,6 +222,8 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         float p[Q];
         gather32<Q, PARITY, SOLIDS>(addr, o, bits, p);
 #endif
+        if (F16) denorm<Q, SOLIDS>(p, bits, RsRing{&rring[j & 3][lc], &rring[(j + 1) & 3][lc],
+                                                    &rring[(j + 2) & 3][lc], ZM_RX});
         Forces Fo;
         if (MULTIPHASE) {
             Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
@@ -223,19 +236,23 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         float rho, ux, uy, uz;
         collide<Q>(kp, p, Fo, rho, ux, uy, uz);
         if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+        if (F16) normalize<Q>(p, __ldg(rown + o.c));
         store32<Q, PARITY, SOLIDS>(addr, o, bits, p);
     }
 }
 
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16>
 __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
                                                                 const uint32_t* __restrict__ nbmask,
-                                                                unsigned* status, int zchunk) {
-    __shared__ float ring[4][ZM_RP];
+                                                                unsigned* status, int zchunk,
+                                                                const float* __restrict__ rsrc,
+                                                                const float* __restrict__ rown) {
+    __shared__ float ring[F16 ? 8 : 4][ZM_RP];
     const KGeom g{kp};
-    const PlanePtrs addr{kp};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
-                                             blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring);
+    const PlanePtrsT<typename std::conditional<F16, __half, float>::type> addr{kp};
+    collide_tile<PARITY, SOLIDS, MULTIPHASE, F16>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
+                                                  blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring, ring + 4,
+                                                  rsrc, rown);
 }
 
 // multi-domain collide-stream pass: one block per tile of any member of the launch's table;
@@ -249,13 +266,21 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc, ring);
+    collide_tile<PARITY, SOLIDS, MULTIPHASE, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
+                                                    ring, nullptr, nullptr, nullptr);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
-__global__ void init_kernel(KParams kp, float* __restrict__ f, const float* __restrict__ rho_in,
-                            const float* __restrict__ u_in, const uint32_t* __restrict__ nbmask) {
+// F16: slot i of x is written relative to the density of x - e_i (x itself where that neighbour
+// is solid), the cell that writes it in the AA streaming; rdst receives the initial densities.
+template <bool F16>
+__global__ void init_kernel(KParams kp, void* __restrict__ fv, const float* __restrict__ rho_in,
+                            const float* __restrict__ u_in, const uint32_t* __restrict__ nbmask,
+                            float* __restrict__ rdst) {
+    using T = typename std::conditional<F16, __half, float>::type;
+    T* f = reinterpret_cast<T*>(fv);
     const long long n = kp.ncell;
+    const long long nxy = (long long)kp.nx * kp.ny;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x) {
         float out[Q];
@@ -299,20 +324,70 @@ __global__ void init_kernel(KParams kp, float* __restrict__ f, const float* __re
                 m[MP<Q>(26)] = cs4 * rho * (uxx + uyy + uzz) + cs6 * rho;
             }
             to_pops<Q>(m, out);
-        }
+            if (F16) {
+                const Cell c = make_cell(kp, (int)(idx % kp.nx), (int)((idx / kp.nx) % kp.ny), (int)(idx / nxy));
+                const uint32_t bits = solid_bits<Q>(kp, nbmask, c);
+                const float* r = rho_in;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i * kp.plane + idx] = out[i];
+                for (int i = 0; i < Q; ++i) {
+                    const bool own = i == 0 || ((bits >> OPP(i)) & 1u);
+                    const float rw = own ? rho : __ldg(r + c.nb(-EX(i), -EY(i), -EZ(i)));
+                    out[i] = out[i] / rw - OMEGA<Q>(i);
+                }
+            }
+        }
+        if (F16) rdst[idx] = solid ? 1.0f : rho_in[idx];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) stpop(f + i * kp.plane + idx, out[i]);
+    }
+}
+
+// ---- shifted FP16 store from natural-order populations (checkpoint restore): densities, then
+// the slot values relative to them
+__global__ void f16_density_kernel(KParams kp, const float* __restrict__ fin, const uint32_t* __restrict__ nbmask,
+                                   float* __restrict__ rdst) {
+    const long long n = kp.ncell;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        float rho = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += fin[i * n + idx];
+        rdst[idx] = (nbmask && (__ldg(nbmask + idx) & 1u)) ? 1.0f : rho;
+    }
+}
+
+__global__ void f16_pack_kernel(KParams kp, const float* __restrict__ fin, const uint32_t* __restrict__ nbmask,
+                                const float* __restrict__ rsrc, __half* __restrict__ f) {
+    const long long n = kp.ncell;
+    const long long nxy = (long long)kp.nx * kp.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const Cell c = make_cell(kp, (int)(idx % kp.nx), (int)((idx / kp.nx) % kp.ny), (int)(idx / nxy));
+        const uint32_t bits = solid_bits<Q>(kp, nbmask, c);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float h = 0.0f;
+            if (!(bits & 1u)) {
+                const bool own = i == 0 || ((bits >> OPP(i)) & 1u);
+                const float rw = own ? __ldg(rsrc + idx) : __ldg(rsrc + c.nb(-EX(i), -EY(i), -EZ(i)));
+                h = fin[i * n + idx] / rw - OMEGA<Q>(i);
+            }
+            f[i * kp.plane + idx] = __float2half_rn(h);
+        }
     }
 }
 
 // ---- macroscopic output: rho, u = (sum f e + F/2)/rho, FP64 block partial sums
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) moments_kernel(KParams kp, const float* __restrict__ f,
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16>
+__global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) moments_kernel(KParams kp, const void* __restrict__ fv,
                                                                        const float* __restrict__ psi,
                                                                        const uint32_t* __restrict__ nbmask,
                                                                        float* __restrict__ rho_out,
                                                                        float* __restrict__ u_out,
-                                                                       double* __restrict__ partials) {
+                                                                       double* __restrict__ partials,
+                                                                       const float* __restrict__ rsrc) {
+    using T = typename std::conditional<F16, __half, float>::type;
+    const T* f = reinterpret_cast<const T*>(fv);
     __shared__ PsiTile<CS_BX, CS_BY, CS_BZ> tile;
     __shared__ double red[4][CS_BX * CS_BY * CS_BZ / 32];
     const int x0 = blockIdx.x * CS_BX, y0 = blockIdx.y * CS_BY, z0 = blockIdx.z * CS_BZ;
@@ -327,7 +402,10 @@ __global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) moments_kernel(KParams 
         c = make_cell(kp, x, y, z);
         bits = SOLIDS ? solid_bits<Q>(kp, nbmask, c) : 0u;
         active = !(bits & 1u);
-        if (active) gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+        if (active) {
+            gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+            if (F16) denorm<Q, SOLIDS>(p, bits, RsCell{rsrc, c});
+        }
     }
     if (MULTIPHASE) {
         tile.load(kp, psi, x0, y0, z0, tid);
@@ -386,9 +464,11 @@ __global__ void __launch_bounds__(CS_BX * CS_BY * CS_BZ) moments_kernel(KParams 
 }
 
 // ---- checkpoint gather: populations of the current state in natural order
-template <int PARITY, bool SOLIDS>
-__global__ void gather_kernel(KParams kp, const float* __restrict__ f, const uint32_t* __restrict__ nbmask,
-                              float* __restrict__ out) {
+template <int PARITY, bool SOLIDS, bool F16>
+__global__ void gather_kernel(KParams kp, const void* __restrict__ fv, const uint32_t* __restrict__ nbmask,
+                              float* __restrict__ out, const float* __restrict__ rsrc) {
+    using T = typename std::conditional<F16, __half, float>::type;
+    const T* f = reinterpret_cast<const T*>(fv);
     const int x = blockIdx.x * PSI_BX + threadIdx.x;
     const int y = blockIdx.y * PSI_BY + threadIdx.y;
     const int z = blockIdx.z;
@@ -401,6 +481,7 @@ __global__ void gather_kernel(KParams kp, const float* __restrict__ f, const uin
         for (int i = 0; i < Q; ++i) p[i] = 0.0f;
     } else {
         gather<Q, PARITY, SOLIDS>(kp, f, c, bits, p);
+        if (F16) denorm<Q, SOLIDS>(p, bits, RsCell{rsrc, c});
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) out[i * kp.ncell + c.idx] = p[i];
@@ -411,10 +492,12 @@ __global__ void gather_kernel(KParams kp, const float* __restrict__ f, const uin
 // wall.  out[0] += such cells, out[1] += liquid cells of the floor layer, out[2..5] = min / max
 // of their x and y.  rho is formed as the moments kernel forms it.
 constexpr int CT_BX = 32, CT_BY = 8;
-template <int PARITY>
-__global__ void __launch_bounds__(CT_BX * CT_BY) contact_kernel(KParams kp, const float* __restrict__ f,
+template <int PARITY, bool F16>
+__global__ void __launch_bounds__(CT_BX * CT_BY) contact_kernel(KParams kp, const void* __restrict__ fv,
                                                               const uint32_t* __restrict__ nbmask, float thr,
-                                                              int* __restrict__ out) {
+                                                              int* __restrict__ out, const float* __restrict__ rsrc) {
+    using T = typename std::conditional<F16, __half, float>::type;
+    const T* f = reinterpret_cast<const T*>(fv);
     const int x = blockIdx.x * CT_BX + threadIdx.x;
     const int y = blockIdx.y * CT_BY + threadIdx.y;
     const int z = blockIdx.z;
@@ -425,6 +508,7 @@ __global__ void __launch_bounds__(CT_BX * CT_BY) contact_kernel(KParams kp, cons
         if (!(bits & 1u) && bits != 0u) {
             float p[Q], m[Q];
             gather<Q, PARITY, true>(kp, f, c, bits, p);
+            if (F16) denorm<Q, true>(p, bits, RsCell{rsrc, c});
             to_moments<Q>(p, m);
             wet = m[0] > thr;
         }
@@ -465,20 +549,65 @@ dim3 cs_grid(const KParams& kp) {
 #ifndef LBM_ZM_CARVEOUT
 #define LBM_ZM_CARVEOUT -1
 #endif
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const float* psi,
-                                   const uint32_t* nbmask, unsigned* status, int zc) {
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16>
+cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const Bufs& B, int zc) {
     if (LBM_ZM_CARVEOUT >= 0) {
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE>,
+            cudaError_t e = cudaFuncSetAttribute(collide_kernel<PARITY, SOLIDS, MULTIPHASE, F16>,
                                                  cudaFuncAttributePreferredSharedMemoryCarveout, LBM_ZM_CARVEOUT);
             if (e != cudaSuccess) return e;
             configured = true;
         }
     }
-    collide_kernel<PARITY, SOLIDS, MULTIPHASE><<<g, b, 0, st>>>(kp, psi, nbmask, status, zc);
+    collide_kernel<PARITY, SOLIDS, MULTIPHASE, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, zc, B.rsrc, B.rnew);
     return cudaGetLastError();
+}
+
+template <bool F16>
+cudaError_t launch_collide_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, const Bufs& B, int zc, int key) {
+    switch (key) {
+        case 0: return launch_collide_variant<0, false, false, F16>(g, b, st, kp, B, zc);
+        case 1: return launch_collide_variant<0, false, true, F16>(g, b, st, kp, B, zc);
+        case 2: return launch_collide_variant<0, true, false, F16>(g, b, st, kp, B, zc);
+        case 3: return launch_collide_variant<0, true, true, F16>(g, b, st, kp, B, zc);
+        case 4: return launch_collide_variant<1, false, false, F16>(g, b, st, kp, B, zc);
+        case 5: return launch_collide_variant<1, false, true, F16>(g, b, st, kp, B, zc);
+        case 6: return launch_collide_variant<1, true, false, F16>(g, b, st, kp, B, zc);
+        default: return launch_collide_variant<1, true, true, F16>(g, b, st, kp, B, zc);
+    }
+}
+
+template <bool F16>
+void launch_psi_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int parity, int solids, const Bufs& B) {
+    if (parity == 0 && !solids) psi_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+    else if (parity == 0) psi_kernel<0, true, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+    else if (!solids) psi_kernel<1, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+    else psi_kernel<1, true, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+}
+
+template <bool F16>
+void launch_moments_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int key, const Bufs& B, float* rho,
+                          float* u, double* partials) {
+    switch (key) {
+        case 0: moments_kernel<0, false, false, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 1: moments_kernel<0, false, true, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 2: moments_kernel<0, true, false, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 3: moments_kernel<0, true, true, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 4: moments_kernel<1, false, false, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 5: moments_kernel<1, false, true, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        case 6: moments_kernel<1, true, false, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+        default: moments_kernel<1, true, true, F16><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, B.rsrc); break;
+    }
+}
+
+template <bool F16>
+void launch_gather_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int parity, int solids, const Bufs& B,
+                         float* out) {
+    if (parity == 0 && !solids) gather_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
+    else if (parity == 0) gather_kernel<0, true, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
+    else if (!solids) gather_kernel<1, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
+    else gather_kernel<1, true, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
 }
 
 }  // namespace
@@ -486,13 +615,10 @@ cudaError_t launch_collide_variant(dim3 g, dim3 b, cudaStream_t st, const KParam
 #define LBM_CAT2(a, b) a##b
 #define LBM_CAT(a, b) LBM_CAT2(a, b)
 
-cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f, float* psi,
-                                         const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B, cudaStream_t st) {
     const dim3 g = psi_grid(kp), b(PSI_BX, PSI_BY);
-    if (parity == 0 && !solids) psi_kernel<0, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
-    else if (parity == 0) psi_kernel<0, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
-    else if (!solids) psi_kernel<1, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
-    else psi_kernel<1, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, status);
+    if (B.f16) launch_psi_store<true>(g, b, st, kp, parity, solids, B);
+    else launch_psi_store<false>(g, b, st, kp, parity, solids, B);
     return cudaGetLastError();
 }
 
@@ -507,22 +633,13 @@ static int collide_zchunk(const KParams& kp) {
     return (int)((kp.nz + chunks - 1) / chunks);
 }
 
-cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, float* f, const float* psi,
-                                             const uint32_t* nbmask, unsigned* status, cudaStream_t st) {
-    (void)f;   // addressed through kp.fq
+cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B,
+                                             cudaStream_t st) {
     const int zc = collide_zchunk(kp);
     const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
-    switch (key) {
-        case 0: return launch_collide_variant<0, false, false>(g, b, st, kp, psi, nbmask, status, zc);
-        case 1: return launch_collide_variant<0, false, true>(g, b, st, kp, psi, nbmask, status, zc);
-        case 2: return launch_collide_variant<0, true, false>(g, b, st, kp, psi, nbmask, status, zc);
-        case 3: return launch_collide_variant<0, true, true>(g, b, st, kp, psi, nbmask, status, zc);
-        case 4: return launch_collide_variant<1, false, false>(g, b, st, kp, psi, nbmask, status, zc);
-        case 5: return launch_collide_variant<1, false, true>(g, b, st, kp, psi, nbmask, status, zc);
-        case 6: return launch_collide_variant<1, true, false>(g, b, st, kp, psi, nbmask, status, zc);
-        default: return launch_collide_variant<1, true, true>(g, b, st, kp, psi, nbmask, status, zc);
-    }
+    return B.f16 ? launch_collide_store<true>(g, b, st, kp, B, zc, key)
+                 : launch_collide_store<false>(g, b, st, kp, B, zc, key);
 }
 
 cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,
@@ -556,51 +673,57 @@ cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams& phys, const BatchD
     return cudaGetLastError();
 }
 
-cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, const float* f, const uint32_t* nbmask,
-                                             float thr, int* out, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, const Bufs& B, float thr, int* out,
+                                             cudaStream_t st) {
     const dim3 g((kp.nx + CT_BX - 1) / CT_BX, (kp.ny + CT_BY - 1) / CT_BY, kp.nz), b(CT_BX, CT_BY);
-    if (parity == 0) contact_kernel<0><<<g, b, 0, st>>>(kp, f, nbmask, thr, out);
-    else contact_kernel<1><<<g, b, 0, st>>>(kp, f, nbmask, thr, out);
+    if (B.f16) {
+        if (parity == 0) contact_kernel<0, true><<<g, b, 0, st>>>(kp, B.f, B.nbmask, thr, out, B.rsrc);
+        else contact_kernel<1, true><<<g, b, 0, st>>>(kp, B.f, B.nbmask, thr, out, B.rsrc);
+    } else {
+        if (parity == 0) contact_kernel<0, false><<<g, b, 0, st>>>(kp, B.f, B.nbmask, thr, out, nullptr);
+        else contact_kernel<1, false><<<g, b, 0, st>>>(kp, B.f, B.nbmask, thr, out, nullptr);
+    }
     return cudaGetLastError();
 }
 
 int LBM_CAT(tile_height_q, LBM_Q)() { return ZM_BY; }
 int LBM_CAT(resident_blocks_q, LBM_Q)() { return ZM_MINB; }
 
-cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, float* f, const float* rho, const float* u,
-                                          const uint32_t* nbmask, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, const Bufs& B, const float* rho, const float* u,
+                                          cudaStream_t st) {
     const long long blocks = (kp.ncell + 255) / 256;
     const int g = (int)(blocks < 152LL * 64 ? blocks : 152LL * 64);
-    init_kernel<<<g, 256, 0, st>>>(kp, f, rho, u, nbmask);
+    if (B.f16) init_kernel<true><<<g, 256, 0, st>>>(kp, B.f, rho, u, B.nbmask, const_cast<float*>(B.rsrc));
+    else init_kernel<false><<<g, 256, 0, st>>>(kp, B.f, rho, u, B.nbmask, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t LBM_CAT(launch_moments_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f,
-                                             const float* psi, const uint32_t* nbmask, float* rho, float* u,
-                                             double* partials, int* nblocks, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_f16_restore_q, LBM_Q)(const KParams& kp, const Bufs& B, const float* fin, cudaStream_t st) {
+    const long long blocks = (kp.ncell + 255) / 256;
+    const int g = (int)(blocks < 152LL * 64 ? blocks : 152LL * 64);
+    float* r = const_cast<float*>(B.rsrc);
+    f16_density_kernel<<<g, 256, 0, st>>>(kp, fin, B.nbmask, r);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    f16_pack_kernel<<<g, 256, 0, st>>>(kp, fin, B.nbmask, r, reinterpret_cast<__half*>(B.f));
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_moments_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B, float* rho,
+                                             float* u, double* partials, int* nblocks, cudaStream_t st) {
     const dim3 g = cs_grid(kp), b(CS_BX, CS_BY, CS_BZ);
     *nblocks = (int)(g.x * g.y * g.z);
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
-    switch (key) {
-        case 0: moments_kernel<0, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 1: moments_kernel<0, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 2: moments_kernel<0, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 3: moments_kernel<0, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 4: moments_kernel<1, false, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 5: moments_kernel<1, false, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        case 6: moments_kernel<1, true, false><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-        default: moments_kernel<1, true, true><<<g, b, 0, st>>>(kp, f, psi, nbmask, rho, u, partials); break;
-    }
+    if (B.f16) launch_moments_store<true>(g, b, st, kp, key, B, rho, u, partials);
+    else launch_moments_store<false>(g, b, st, kp, key, B, rho, u, partials);
     return cudaGetLastError();
 }
 
-cudaError_t LBM_CAT(launch_gather_q, LBM_Q)(const KParams& kp, int parity, int solids, const float* f,
-                                            const uint32_t* nbmask, float* out, cudaStream_t st) {
+cudaError_t LBM_CAT(launch_gather_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B, float* out,
+                                            cudaStream_t st) {
     const dim3 g = psi_grid(kp), b(PSI_BX, PSI_BY);
-    if (parity == 0 && !solids) gather_kernel<0, false><<<g, b, 0, st>>>(kp, f, nbmask, out);
-    else if (parity == 0) gather_kernel<0, true><<<g, b, 0, st>>>(kp, f, nbmask, out);
-    else if (!solids) gather_kernel<1, false><<<g, b, 0, st>>>(kp, f, nbmask, out);
-    else gather_kernel<1, true><<<g, b, 0, st>>>(kp, f, nbmask, out);
+    if (B.f16) launch_gather_store<true>(g, b, st, kp, parity, solids, B, out);
+    else launch_gather_store<false>(g, b, st, kp, parity, solids, B, out);
     return cudaGetLastError();
 }
 

@@ -11,8 +11,14 @@
 // second copy.  Half-way bounce-back: on an odd step a link to a solid
 // neighbour reads/writes the cell's own slot instead (f_i(x) <- slot i of x,
 // f*_i -> slot ibar of x); an even step is local and needs no test.
+//
+// Shifted FP16 store (optional): a slot holds h = f / rho_w - omega_i in half precision,
+// rho_w being the density of the cell that wrote it, kept in FP32 in a density field.  The
+// population f_i arriving at x was written by x - e_i (by x itself where that neighbour is
+// solid), so the reader multiplies (omega_i + h) by that cell's density.  All arithmetic is FP32.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <climits>
@@ -48,6 +54,21 @@ __host__ __device__ constexpr float WN(int i) {
          : (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 3 ? 1.0f / 72.0f
          : 0.0f;
 }
+
+// lattice weights omega_i (Eq. e5; D3Q19: 1/3, 1/18, 1/36 of App. C)
+template <int Q>
+__host__ __device__ constexpr float OMEGA(int i) {
+    return (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 0 ? (Q == 27 ? 8.0f / 27.0f : 1.0f / 3.0f)
+         : (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 1 ? (Q == 27 ? 2.0f / 27.0f : 1.0f / 18.0f)
+         : (EX(i) * EX(i) + EY(i) * EY(i) + EZ(i) * EZ(i)) == 2 ? (Q == 27 ? 1.0f / 54.0f : 1.0f / 36.0f)
+         : 1.0f / 216.0f;
+}
+
+// population slot loads / stores in either storage type (FP32 values or FP16 shifted values)
+__device__ __forceinline__ float ldpop(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldpop(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void stpop(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stpop(__half* p, float v) { *p = __float2half_rn(v); }
 
 template <int Q>
 __device__ __forceinline__ void to_moments(const float (&f)[Q], float (&m)[Q]);
@@ -115,36 +136,57 @@ __device__ __forceinline__ uint32_t solid_bits(const KParams& kp, const uint32_t
     return bits;
 }
 
-// ------------------------------------------------------------------ AA gather / store
-template <int Q, int PARITY, bool SOLIDS>
-__device__ __forceinline__ void gather(const KParams& kp, const float* __restrict__ f, const Cell& c, uint32_t bits,
+// ------------------------------------------------------------------ AA gather (raw slot values)
+template <int Q, int PARITY, bool SOLIDS, class T>
+__device__ __forceinline__ void gather(const KParams& kp, const T* __restrict__ f, const Cell& c, uint32_t bits,
                                        float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            p[i] = __ldg(f + i * kp.plane + c.idx);
+            p[i] = ldpop(f + i * kp.plane + c.idx);
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
-            p[i] = __ldg(f + i * kp.plane + c.idx);   // reflected at the wall in the previous step
+            p[i] = ldpop(f + i * kp.plane + c.idx);   // reflected at the wall in the previous step
         } else {
-            p[i] = __ldg(f + OPP(i) * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
+            p[i] = ldpop(f + OPP(i) * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
         }
     }
 }
 
-template <int Q, int PARITY, bool SOLIDS>
-__device__ __forceinline__ void store(const KParams& kp, float* __restrict__ f, const Cell& c, uint32_t bits,
-                                      const float (&p)[Q]) {
+// Shifted FP16 store: slot values -> populations.  rs.at(dx, dy, dz) is the density of cell
+// x + (dx, dy, dz) in the density field the slots were written with.
+template <int Q, bool SOLIDS, class RS>
+__device__ __forceinline__ void denorm(float (&p)[Q], uint32_t bits, const RS& rs) {
+    const float self = rs.at(0, 0, 0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (PARITY == 0 || i == 0) {
-            f[OPP(i) * kp.plane + c.idx] = p[i];
-        } else if (SOLIDS && ((bits >> i) & 1u)) {
-            f[OPP(i) * kp.plane + c.idx] = p[i];       // half-way bounce-back
-        } else {
-            f[i * kp.plane + c.nb(EX(i), EY(i), EZ(i))] = p[i];
-        }
+        const bool own = i == 0 || (SOLIDS && ((bits >> OPP(i)) & 1u));
+        const float r = own ? self : rs.at(-EX(i), -EY(i), -EZ(i));
+        p[i] = (OMEGA<Q>(i) + p[i]) * r;
     }
 }
+
+// ... and populations -> slot values of a cell of density rho
+template <int Q>
+__device__ __forceinline__ void normalize(float (&p)[Q], float rho) {
+    const float inv = 1.0f / rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) p[i] = p[i] * inv - OMEGA<Q>(i);
+}
+
+// density field lookups for denorm: three ring planes in shared memory, a 32-bit neighbourhood,
+// or a 64-bit one
+struct RsRing {
+    const float *pm, *p0, *pp;
+    int sy;
+    __device__ __forceinline__ float at(int dx, int dy, int dz) const {
+        return (dz < 0 ? pm : (dz > 0 ? pp : p0))[dx + dy * sy];
+    }
+};
+struct RsCell {
+    const float* r;
+    const Cell& c;
+    __device__ __forceinline__ float at(int dx, int dy, int dz) const { return __ldg(r + c.nb(dx, dy, dz)); }
+};
 
 // ------------------------------------------------------------------ equation of state -> psi
 // psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. II C).  The Carnahan-Starling
@@ -353,11 +395,14 @@ __device__ __forceinline__ uint32_t solid_bits32(const GM& g, const uint32_t* __
 }
 
 // Address of cell offset `off` in population plane i: per-plane base pointers from the kernel
-// parameters (constant bank, free operands) for single-domain launches ...
-struct PlanePtrs {
+// parameters (constant bank, free operands) for single-domain launches (T = float, or __half for
+// the shifted FP16 store) ...
+template <class T>
+struct PlanePtrsT {
     const KParams& kp;
-    __device__ __forceinline__ float* ptr(int i, uint32_t off) const { return kp.fq[i] + off; }
+    __device__ __forceinline__ T* ptr(int i, uint32_t off) const { return reinterpret_cast<T*>(kp.fq[i]) + off; }
 };
+using PlanePtrs = PlanePtrsT<float>;
 // ... or, for multi-domain launches, one base pointer and a 32-bit plane stride: the whole
 // index i * plane + off stays in 32 bits (a member's Q planes hold < 2^32 floats), so each access
 // costs one integer multiply-add and one wide address computation.
@@ -378,16 +423,22 @@ struct PlaneStride64 {
     }
 };
 
+struct RsOff32 {
+    const float* r;
+    const Off32& o;
+    __device__ __forceinline__ float at(int dx, int dy, int dz) const { return __ldg(r + o.nb(dx, dy, dz)); }
+};
+
 template <int Q, int PARITY, bool SOLIDS, class A>
 __device__ __forceinline__ void gather32(const A& a, const Off32& o, uint32_t bits, float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            p[i] = __ldg(a.ptr(i, o.c));
+            p[i] = ldpop(a.ptr(i, o.c));
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
-            p[i] = __ldg(a.ptr(i, o.c));
+            p[i] = ldpop(a.ptr(i, o.c));
         } else {
-            p[i] = __ldg(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
+            p[i] = ldpop(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
         }
     }
 }
@@ -397,11 +448,11 @@ __device__ __forceinline__ void store32(const A& a, const Off32& o, uint32_t bit
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0) {
-            *a.ptr(OPP(i), o.c) = p[i];
+            stpop(a.ptr(OPP(i), o.c), p[i]);
         } else if (SOLIDS && ((bits >> i) & 1u)) {
-            *a.ptr(OPP(i), o.c) = p[i];
+            stpop(a.ptr(OPP(i), o.c), p[i]);
         } else {
-            *a.ptr(i, o.nb(EX(i), EY(i), EZ(i))) = p[i];
+            stpop(a.ptr(i, o.nb(EX(i), EY(i), EZ(i))), p[i]);
         }
     }
 }

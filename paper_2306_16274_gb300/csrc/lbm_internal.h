@@ -66,29 +66,43 @@ struct BatchTile {
     int d, x0, y0, z0, zc;
 };
 
+// Device buffers of one context's launches.  f: the population slots, floats or (f16) the
+// shifted FP16 store; rsrc: the densities the stored slots were written with; rnew: the other
+// density buffer (the density pass writes it, the collide pass writes relative to it).
+struct Bufs {
+    void* f;
+    float* psi;
+    const uint32_t* nbmask;
+    unsigned* status;
+    int f16;
+    const float* rsrc;
+    float* rnew;
+};
+
 // Launchers (one set per lattice).  parity: 0 = natural layout (even AA step),
 // 1 = swapped layout (odd AA step).  solids: walls or a solid mask exist.
 #define LBM_DECLARE_LAUNCHERS(Q)                                                                    \
-    cudaError_t launch_psi_q##Q(const KParams& kp, int parity, int solids, const float* f,          \
-                                float* psi, const uint32_t* nbmask, unsigned* status, cudaStream_t st); \
-    cudaError_t launch_collide_q##Q(const KParams& kp, int parity, int solids, float* f,             \
-                                    const float* psi, const uint32_t* nbmask, unsigned* status,      \
+    cudaError_t launch_psi_q##Q(const KParams& kp, int parity, int solids, const Bufs& B,           \
+                                cudaStream_t st);                                                   \
+    cudaError_t launch_collide_q##Q(const KParams& kp, int parity, int solids, const Bufs& B,       \
                                     cudaStream_t st);                                               \
-    cudaError_t launch_init_q##Q(const KParams& kp, float* f, const float* rho, const float* u,     \
-                                 const uint32_t* nbmask, cudaStream_t st);                          \
-    cudaError_t launch_moments_q##Q(const KParams& kp, int parity, int solids, const float* f,      \
-                                    const float* psi, const uint32_t* nbmask, float* rho, float* u,  \
-                                    double* partials, int* nblocks, cudaStream_t st);               \
-    cudaError_t launch_gather_q##Q(const KParams& kp, int parity, int solids, const float* f,       \
-                                   const uint32_t* nbmask, float* out, cudaStream_t st);              \
+    cudaError_t launch_init_q##Q(const KParams& kp, const Bufs& B, const float* rho, const float* u, \
+                                 cudaStream_t st);                                                  \
+    cudaError_t launch_f16_restore_q##Q(const KParams& kp, const Bufs& B, const float* fin,         \
+                                        cudaStream_t st);                                           \
+    cudaError_t launch_moments_q##Q(const KParams& kp, int parity, int solids, const Bufs& B,       \
+                                    float* rho, float* u, double* partials, int* nblocks,            \
+                                    cudaStream_t st);                                               \
+    cudaError_t launch_gather_q##Q(const KParams& kp, int parity, int solids, const Bufs& B,        \
+                                   float* out, cudaStream_t st);                                     \
     cudaError_t launch_collide_batch_q##Q(const KParams& phys, const BatchDomTable& tab,             \
                                           const BatchTile* tiles, int ntiles, int parity, int solids,  \
                                           cudaStream_t st);                                           \
     cudaError_t launch_psi_batch_q##Q(const KParams& phys, const BatchDomTable& tab,                 \
                                       const BatchTile* tiles, int ntiles, int parity, int solids,      \
                                       cudaStream_t st);                                               \
-    cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const float* f,                  \
-                                    const uint32_t* nbmask, float thr, int* out, cudaStream_t st);   \
+    cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const Bufs& B, float thr, int* out, \
+                                    cudaStream_t st);                                               \
     int tile_height_q##Q();                                                                         \
     int resident_blocks_q##Q();
 

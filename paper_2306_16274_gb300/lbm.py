@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "liblbm.so")
 
 EOS = {"none": 0, "cs": 1, "piecewise": 2}
+STORE = {"fp32": 0, "fp16": 1}
 BC = {"periodic": 0, "wall": 1}
 RATE_NAMES = ("s0", "s1", "s2", "s2b", "s3", "s3b", "s4", "s4b", "s5", "s6")
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_UNSTABLE",
@@ -37,6 +38,7 @@ class lbm_params(ctypes.Structure):
         ("s", ctypes.c_double * 10), ("variable_nu", ctypes.c_int32),
         ("nu_l", ctypes.c_double), ("nu_v", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
         ("g", ctypes.c_double * 3), ("psi_fp64_rho", ctypes.c_double), ("zchunk", ctypes.c_int32),
+        ("store", ctypes.c_int32),
     ]
 
 
@@ -94,7 +96,8 @@ def lib():
 class Params:
     """Mirror of lbm_params.  shape = (nx, ny, nz); bc per axis "periodic" / "wall";
     eos "none" / "cs" (eos_p = a, b, R, T) / "piecewise" (rho1, rho2, theta_v, theta_m, theta_l);
-    rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library)."""
+    rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library);
+    store "fp32" or "fp16" (shifted FP16 population store)."""
     lattice: int = 19
     shape: tuple = (32, 32, 32)
     bc: tuple = ("periodic", "periodic", "periodic")
@@ -113,6 +116,7 @@ class Params:
     g: tuple = (0.0, 0.0, 0.0)
     psi_fp64_rho: float = -1.0
     zchunk: int = 0
+    store: str = "fp32"
 
     def to_c(self):
         c = lbm_params()
@@ -135,6 +139,7 @@ class Params:
             c.g[k] = float(self.g[k])
         c.psi_fp64_rho = float(self.psi_fp64_rho)
         c.zchunk = int(self.zchunk)
+        c.store = STORE[self.store] if isinstance(self.store, str) else int(self.store)
         return c
 
     @property

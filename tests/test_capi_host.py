@@ -54,6 +54,7 @@ def test_params_struct_layout_matches_header(lib):
     (dict(eos="piecewise", eos_p=(0.5, 0.1, 0.1, -0.01, 0.3)), "rho1"),
     (dict(variable_nu=True, nu_l=0.01, nu_v=0.01, rho_l=1.0, rho_v=1.0), "variable"),
     (dict(bc=(0, 2, 0)), "bc"),
+    (dict(store=2), "store"),
 ])
 def test_invalid_parameters_are_rejected(lib, change, msg):
     kw = dict(lattice=19, shape=(4, 4, 4))
@@ -116,3 +117,14 @@ def test_estimate_bytes_counts_the_resident_state(lib):
 def test_contact_rejects_null_context(lib):
     out = (ctypes.c_int32 * 6)()
     assert lib.lbm_contact(None, ctypes.c_float(0.5), out, 0) == 1
+
+
+def test_estimate_bytes_fp16_store(lib):
+    # half-precision slots plus two FP32 density fields
+    nx, ny, nz = 40, 36, 24
+    n = nx * ny * nz
+    plane = (n + 63) // 64 * 64
+    blocks = -(-nx // 32) * -(-ny // 4) * -(-nz // 2)
+    for Q in (19, 27):
+        want = Q * plane * 2 + 2 * 4 * n + n * 4 + 64 + blocks * 32 + 32
+        assert L.estimate_bytes(L.Params(lattice=Q, shape=(nx, ny, nz), store="fp16")) == want
