@@ -336,7 +336,7 @@ SERVE_WORKLOAD = ("request stream of {n} jobs (numpy seed 2306): by fair coin dr
                   "(Sec. IV B; edge L ~ U{{64..160}}, R0 = L/6, R/R0 ~ U[0.2, 2], cylinder on the bottom wall along y, "
                   "walls in z, G_ads = 0.23, We = 10 from the oracle's Laplace surface tension, nu = 0.05, tanh width 3, "
                   "run until "
-                  "the droplet leaves the solid or 4 capillary times) or a static droplet of a kappa sweep "
+                  "the droplet has left the solid for 0.3 capillary times, at most 4 capillary times) or a static droplet of a kappa sweep "
                   "(periodic L^3, R ~ U[L/8, L/4], kappa in 0..0.6, 2000 steps); lattice D3Q19/D3Q27 by fair coin; "
                   "C-S at 0.7 T_c, sigma = 0.1; ticks of 100 steps; budget 150 GB")
 
@@ -363,7 +363,7 @@ def serving_specs(n_jobs, rate, seed=2306):
             f = (rho.astype(np.float32), u.astype(np.float32), solid)
             specs.append(JobSpec(name=j["name"], params=p, make_fields=lambda f=f: f, steps=int(4 * tau),
                                  stop_on_detach=True, threshold=0.5 * (rl + rv), arrival=j["arrival"],
-                                 has_solid=True))
+                                 has_solid=True, detach_hold=int(0.3 * tau)))
         else:
             p = Params(lattice=j["lattice"], shape=j["shape"], kappa=0.15 * (k % 5), **eos)
             rho, u = W.droplet(j["shape"], j["R"], rl, rv)

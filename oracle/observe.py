@@ -9,7 +9,9 @@ reading used throughout:
 * a fluid cell touches a solid when one of its lattice neighbours x + e_i (the active
   lattice's velocities, i != 0) is a solid cell of the mask or lies beyond a wall;
 * contact: at least one liquid cell touches a solid; the contact time runs from the first
-  step with contact to the first later step without;
+  step with contact to the first later step without contact that stays without contact for
+  `hold` steps (a hydrophobic wall can hold a spreading film one cell above it on a vapour
+  cushion for a while before the droplet leaves; hold = 0 takes the first step without);
 * the footprint on a bottom wall is the set of liquid cells in the layer z = 0; the
   spreading diameter D_f is the mean of its x and y extents (cells).
 
@@ -63,15 +65,22 @@ def spreading_diameter(c):
     return 0.5 * ((c[3] - c[2] + 1) + (c[5] - c[4] + 1))
 
 
-def contact_time(wet_counts, steps):
+def contact_time(wet_counts, steps, hold=0):
     """(touch, detach) steps from a series of wet-cell counts taken at `steps`: touch = first
-    step with wet > 0, detach = first later step with wet == 0 (None where not reached)."""
-    touch = detach = None
+    step with wet > 0; detach = the first later step with wet == 0 from which the counts stay
+    0 for at least `hold` steps (None where not reached)."""
+    touch = None
+    zero_from = None
     for w, t in zip(wet_counts, steps):
         if touch is None:
             if w > 0:
                 touch = t
-        elif w == 0:
-            detach = t
-            break
-    return touch, detach
+            continue
+        if w > 0:
+            zero_from = None
+            continue
+        if zero_from is None:
+            zero_from = t
+        if t - zero_from >= hold:
+            return touch, zero_from
+    return touch, None

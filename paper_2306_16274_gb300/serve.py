@@ -32,8 +32,10 @@ from .lbm import CONTACT_FIELDS, Batch, LBMError, Simulation, estimate_bytes
 class JobSpec:
     """One request.  make_fields() returns (rho, u, solid) host arrays in the library's layout
     (solid may be None).  The job runs until `steps` (rounded up to whole ticks) or, if
-    stop_on_detach, until the first tick without liquid-solid contact after one with contact.
-    threshold: liquid density threshold of the contact detector (None: no detector)."""
+    stop_on_detach, until it has detached: after a tick with liquid-solid contact, a tick without
+    from which the detector stays without contact for `detach_hold` steps (the detachment step is
+    the first of those ticks).  threshold: liquid density threshold of the contact detector
+    (None: no detector)."""
     name: str
     params: object
     make_fields: object
@@ -42,6 +44,7 @@ class JobSpec:
     threshold: float = None
     arrival: float = 0.0
     has_solid: bool = False
+    detach_hold: int = 0
 
 
 @dataclass
@@ -73,6 +76,7 @@ class _Slot:
         self.spec, self.handle, self.nbytes, self.result = spec, handle, nbytes, result
         self.step = 0
         self.done = False
+        self.zero_from = None     # first tick of the current run without contact
 
 
 class Server:
@@ -156,8 +160,14 @@ class Server:
                     if r.touch is None:
                         if wet > 0:
                             r.touch = s.step
-                    elif r.detach is None and wet == 0:
-                        r.detach = s.step
+                    elif r.detach is None:
+                        if wet > 0:
+                            s.zero_from = None
+                        else:
+                            if s.zero_from is None:
+                                s.zero_from = s.step
+                            if s.step - s.zero_from >= s.spec.detach_hold:
+                                r.detach = s.zero_from
                 if s.step >= s.spec.steps or (s.spec.stop_on_detach and r.detach is not None):
                     s.done = True
             still = []

@@ -97,3 +97,10 @@ def test_contact_time_sequence():
     assert observe.contact_time([0, 0, 4, 9, 0, 3], steps) == (20, 40)
     assert observe.contact_time([0, 1, 2, 3, 4, 5], steps) == (10, None)
     assert observe.contact_time([0] * 6, steps) == (None, None)
+    # a lift-off shorter than the hold is not a detachment; the final one is, from its start
+    steps = list(range(0, 120, 10))
+    wet = [0, 5, 7, 0, 0, 6, 4, 0, 0, 0, 0, 0]
+    assert observe.contact_time(wet, steps, hold=0) == (10, 30)
+    assert observe.contact_time(wet, steps, hold=20) == (10, 70)
+    assert observe.contact_time(wet, steps, hold=40) == (10, 70)
+    assert observe.contact_time(wet, steps, hold=50) == (10, None)

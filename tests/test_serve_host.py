@@ -70,9 +70,9 @@ class FakeEngine:
         return (float(h["step"]), 0.0, 0.0, float(len(h["spec"].name))), None
 
 
-def job(name, ncell, steps, schedule=(), arrival=0.0, detach=True):
+def job(name, ncell, steps, schedule=(), arrival=0.0, detach=True, hold=0):
     return JobSpec(name=name, params=FakeParams(ncell), make_fields=list(schedule), steps=steps,
-                   stop_on_detach=detach, threshold=0.5 if schedule else None, arrival=arrival)
+                   stop_on_detach=detach, threshold=0.5 if schedule else None, arrival=arrival, detach_hold=hold)
 
 
 def serve(specs, budget, tick=10, max_active=64):
@@ -111,6 +111,16 @@ def test_retire_at_detachment_or_cap():
     assert (r["stick"].touch, r["stick"].detach, r["stick"].steps) == (20, None, 60)
     assert r["cap_only"].steps == 40                         # rounded up to whole ticks
     assert r["cap_only"].contacts == [] and r["bounce"].contacts[2][:2] == (30, 7)
+
+
+def test_detachment_needs_a_sustained_lift_off():
+    # a short lift-off (one tick) is ignored with a 20-step hold; the final one counts from its start,
+    # and the job stops once the hold has passed
+    specs = [job("cushion", 100, 1000, schedule=[0, 3, 0, 4, 0, 0, 0, 0, 2], hold=20)]
+    r = serve(specs, budget=10 ** 9)[0][0]
+    assert (r.touch, r.detach, r.steps) == (20, 50, 70)
+    r = serve([job("cushion0", 100, 1000, schedule=[0, 3, 0, 4, 0, 0, 0, 0, 2], hold=0)], budget=10 ** 9)[0][0]
+    assert (r.touch, r.detach, r.steps) == (20, 30, 30)
 
 
 def test_results_do_not_depend_on_the_mix():
