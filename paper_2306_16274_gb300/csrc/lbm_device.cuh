@@ -465,27 +465,36 @@ __device__ __forceinline__ Forces stencil_forces3(const KParams& kp, const float
     const float pc = p0[0];
     float Sx = 0.f, Sy = 0.f, Sz = 0.f, Ax = 0.f, Ay = 0.f, Az = 0.f;
     float qxx = 0.f, qyy = 0.f, qzz = 0.f, qxy = 0.f, qxz = 0.f, qyz = 0.f;
+    float pn[Q];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const float* pl = EZ(i) < 0 ? pm : (EZ(i) > 0 ? pp : p0);
-        float pn = pl[EX(i) + EY(i) * sy];
-        if (SOLIDS && ((bits >> i) & 1u)) {
-            pn = pc;
+        pn[i] = pl[EX(i) + EY(i) * sy];
+        if (SOLIDS && ((bits >> i) & 1u)) {   // a solid neighbour: psi(x) there, and F_ads
+            pn[i] = pc;
             Ax += WN<Q>(i) * EX(i);
             Ay += WN<Q>(i) * EY(i);
             Az += WN<Q>(i) * EZ(i);
         }
-        const float wp = WN<Q>(i) * pn;
-        if (EX(i)) Sx += EX(i) > 0 ? wp : -wp;
-        if (EY(i)) Sy += EY(i) > 0 ? wp : -wp;
-        if (EZ(i)) Sz += EZ(i) > 0 ? wp : -wp;
-        const float wd = WN<Q>(i) * (pn - pc);
-        if (EX(i)) qxx += wd;
-        if (EY(i)) qyy += wd;
-        if (EZ(i)) qzz += wd;
-        if (EX(i) && EY(i)) qxy += (EX(i) * EY(i) > 0) ? wd : -wd;
-        if (EX(i) && EZ(i)) qxz += (EX(i) * EZ(i) > 0) ? wd : -wd;
-        if (EY(i) && EZ(i)) qyz += (EY(i) * EZ(i) > 0) ? wd : -wd;
+    }
+    // opposite links together: w e (psi_i - psi_ibar) for F_int, w e e (psi_i + psi_ibar - 2 psi(x))
+    // for Q (e_ibar = -e_i, equal weights)
+    const float pc2 = 2.0f * pc;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (OPP(i) < i) continue;
+        const float a = pn[i] - pn[OPP(i)];
+        const float b = (pn[i] + pn[OPP(i)]) - pc2;
+        const float w = WN<Q>(i);
+        if (EX(i)) Sx += (EX(i) > 0 ? w : -w) * a;
+        if (EY(i)) Sy += (EY(i) > 0 ? w : -w) * a;
+        if (EZ(i)) Sz += (EZ(i) > 0 ? w : -w) * a;
+        if (EX(i)) qxx += w * b;
+        if (EY(i)) qyy += w * b;
+        if (EZ(i)) qzz += w * b;
+        if (EX(i) && EY(i)) qxy += (EX(i) * EY(i) > 0 ? w : -w) * b;
+        if (EX(i) && EZ(i)) qxz += (EX(i) * EZ(i) > 0 ? w : -w) * b;
+        if (EY(i) && EZ(i)) qyz += (EY(i) * EZ(i) > 0 ? w : -w) * b;
     }
     Forces F;
     const float gp = -kp.G * pc;
