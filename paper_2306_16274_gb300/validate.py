@@ -13,6 +13,9 @@ EOS with rho_v = 0.001, rho_l = 1 (Eqs. e19-e21), G = -1, sigma = 0.1.
   X6  capillary-wave periods vs the dispersion relation (Sec. III C, Fig. 2c)
   X7  spatial convergence of the steady densities (Sec. III D; meshes 100-300 instead of 100-400)
   X8  contact time of a droplet bouncing off a super-hydrophobic wall (Sec. III E, Eq. e24)
+  C3  droplet impact on a wall at full size (400 x 400 x 200, R0 = 50): spreading diameter with
+      FP32 populations and with the shifted-FP16 store (the 4x down-scaled copy is compared with
+      the oracle in tests/test_gpu_impact_curve.py)
 
     python -m paper_2306_16274_gb300.validate [--quick] [--cases X1,X5,...]
 
@@ -322,10 +325,42 @@ def contact_time(quick, gamma):
     return out
 
 
+# ---------------------------------------------------------------- C3 full-size impact, FP32 vs FP16
+def impact_fp16(quick):
+    """D3Q19 impact on a neutral wall (G_ads = 0), U = 0.08, nu = 0.05, s4 = STABLE_S4, droplet two
+    cells above the wall: D_f / R0 every R0 / (4 U) steps up to t* = U t / R0 = 3, both stores."""
+    R0 = 12.5 if quick else 50.0
+    shape = (100, 100, 50) if quick else (400, 400, 200)
+    U, nu = 0.08, 0.05
+    every = int(round(R0 / (4 * U)))
+    every += every % 2
+    n = int(3 * R0 / U / every)
+    rho = sphere(shape, R0, centre=(shape[0] / 2.0, shape[1] / 2.0, R0 + 2.0))
+    u = np.zeros((3,) + rho.shape)
+    u[2] = -U * np.clip((rho - RHO_V) / (RHO_L - RHO_V), 0, 1)
+    thr = 0.5 * (RHO_L + RHO_V)
+    curves = {}
+    for store in ("fp32", "fp16"):
+        sim = start(params(19, shape, nu=nu, bc=(0, 0, 1), s4=STABLE_S4, store=store), rho, u)
+        df = []
+        for _ in range(n):
+            sim.step(every)
+            c = sim.contact(thr)
+            df.append(0.0 if c["floor"] == 0 else 0.5 * ((c["xmax"] - c["xmin"] + 1) + (c["ymax"] - c["ymin"] + 1)))
+        sim.close()
+        curves[store] = df
+    a, b = np.array(curves["fp32"]), np.array(curves["fp16"])
+    return {"shape": shape, "R0": R0, "U": U, "nu": nu, "every": every,
+            "t_star": [round(U * every * (k + 1) / R0, 3) for k in range(n)],
+            "Df_over_R0_fp32": [round(v / R0, 4) for v in curves["fp32"]],
+            "Df_over_R0_fp16": [round(v / R0, 4) for v in curves["fp16"]],
+            "max_abs_diff_cells": float(np.abs(a - b).max())}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="smaller boxes and fewer steps")
-    ap.add_argument("--cases", default="X1,X2,X4,X5,X5_27,X6,X7,X8")
+    ap.add_argument("--cases", default="X1,X2,X4,X5,X5_27,X6,X7,X8,C3")
     a = ap.parse_args(argv)
     want = set(a.cases.split(","))
     report = {"printed": PRINTED, "quick": a.quick}
@@ -358,6 +393,8 @@ def main(argv=None):
         guarded("X7", lambda q: {"X7": convergence(q)}, a.quick)
     if "X8" in want:
         guarded("X8", lambda q: {"X8": contact_time(q, gammas[0.0])}, a.quick)
+    if "C3" in want:
+        guarded("C3", lambda q: {"C3": impact_fp16(q)}, a.quick)
     report["seconds"] = time.time() - t0
     print(json.dumps(report), flush=True)
     return report
