@@ -215,9 +215,10 @@ def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None, store="fp3
     return out
 
 
-def run_e2e(Q, rho, u, wparams, steps):
+def run_e2e(Q, rho, u, wparams, steps, dist=None, ws=1):
     """Same metric through the public API with host buffers: pinned host -> device fields,
-    `steps` steps, device -> host moments and sums, timed by the host clock around the whole job."""
+    `steps` steps, device -> host moments and sums, timed by the host clock around the whole job
+    (every rank its own replica between barriers; whole-job rate over the slowest rank)."""
     import torch
 
     from paper_2306_16274_gb300 import Params, Simulation
@@ -231,16 +232,19 @@ def run_e2e(Q, rho, u, wparams, steps):
     import ctypes
     sums = (ctypes.c_double * 4)()
     torch.cuda.synchronize()
+    barrier(dist)
     t0 = time.perf_counter()
     sim.init_fields(rho_h, u_h)
     sim.step(steps)
     sim.moments_into(rho_o, u_o, sums)
     t1 = time.perf_counter()
+    barrier(dist)
     sim.close()
+    seconds = max_over_ranks(dist, t1 - t0)
     h2d = 4 * n * 4
     d2h = 4 * n * 4 + 4 * 8
-    return dict(value=n * steps / (t1 - t0) / 1e6, unit=UNIT, h2d_bytes_per_step=h2d / steps,
-                d2h_bytes_per_step=d2h / steps, seconds=t1 - t0)
+    return dict(value=ws * n * steps / seconds / 1e6, unit=UNIT, h2d_bytes_per_step=h2d / steps,
+                d2h_bytes_per_step=d2h / steps, seconds=seconds)
 
 
 # ---------------------------------------------------------------- batched jobs
@@ -550,12 +554,15 @@ def main():
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(dist, r19["ms"])
     value = whole_job_mlups(ws, n, args.steps, ms)
-    r27 = None if args.no_q27 else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
-    e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps)
-    f16 = {} if args.no_fp16 else {Q: run_lattice(Q, rho, u, wparams, args.steps, args.warmup, dist, store="fp16")
+    # the side legs characterise one GPU; with several ranks only the headline and e2e run
+    single = ws == 1
+    r27 = None if (args.no_q27 or not single) else run_lattice(27, rho, u, wparams, args.steps, args.warmup, dist)
+    e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps, dist, ws)
+    f16 = {} if (args.no_fp16 or not single) else {
+        Q: run_lattice(Q, rho, u, wparams, args.steps, args.warmup, dist, store="fp16")
                                    for Q in ((19,) if args.no_q27 else (19, 27))}
-    batched = None if (args.no_batched or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
-    serving = None if (args.no_serving or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
+    batched = None if (args.no_batched or not single or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
+    serving = None if (args.no_serving or not single or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
     if rank != 0:
         return
     ab = algorithmic_bytes(19)
