@@ -67,14 +67,6 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, float*
                                     blockIdx.y * PSI_BY + threadIdx.y, blockIdx.z, blockIdx.z + 1, rsrc, rdst);
 }
 
-// member population addressing of the multi-domain kernels
-#ifdef LBM_BATCH_ADDR64
-using BatchAddr = PlaneStride64;
-using BatchAddrStride = long long;
-#else
-using BatchAddr = PlaneIdx32;
-using BatchAddrStride = uint32_t;
-#endif
 
 // multi-domain density + psi pass: one block per tile of any member of the launch's table;
 // physics by value
@@ -85,7 +77,7 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParam
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
-    const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
+    const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
     psi_column<PARITY, SOLIDS, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x,
                                       t.y0 + threadIdx.y, t.z0, min(t.z0 + t.zc, m.nz), nullptr, nullptr);
 }
@@ -265,7 +257,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
-    const BatchAddr addr{m.base, (BatchAddrStride)m.plane};
+    const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
     collide_tile<PARITY, SOLIDS, MULTIPHASE, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
                                                     ring, nullptr, nullptr, nullptr);
 }

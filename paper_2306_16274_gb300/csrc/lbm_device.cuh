@@ -414,15 +414,6 @@ struct PlaneIdx32 {
     }
 };
 
-// 64-bit variant of the same (tuning alternative, LBM_BATCH_ADDR64).
-struct PlaneStride64 {
-    const float* base;
-    long long plane;
-    __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
-        return const_cast<float*>(base) + (long long)i * plane + off;
-    }
-};
-
 struct RsOff32 {
     const float* r;
     const Off32& o;
