@@ -40,12 +40,15 @@ WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves th
             "sigma=0.1, G=-1, the paper's default rates, FP32 populations (AA in place)")
 
 
-def algorithmic_bytes(Q, store="fp32"):
+def algorithmic_bytes(Q, store="fp32", onepass=False):
     """Bytes per cell update that the method must move: collide-stream reads and writes the Q
     populations and reads psi once (8Q + 4); the density/psi pass reads the Q populations and
     writes psi (4Q + 4).  Shifted FP16 store: 2-byte slots, and the density field the slots are
     relative to is read by both passes and written by the density pass (collide 4Q + 12,
-    density/psi 2Q + 12)."""
+    density/psi 2Q + 12).  One-pass stepping over two copies: the Q populations read and written
+    once (8Q); psi never leaves the chip."""
+    if onepass:
+        return {"collide": 8 * Q, "psi": 0, "step": 8 * Q}
     if store == "fp16":
         return {"collide": 4 * Q + 12, "psi": 2 * Q + 12, "step": 6 * Q + 24}
     return {"collide": 8 * Q + 4, "psi": 4 * Q + 4, "step": 12 * Q + 8}
@@ -173,11 +176,11 @@ def whole_job_mlups(world_size, cells, steps, ms_max):
 
 
 # ---------------------------------------------------------------- our arm
-def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None, store="fp32"):
+def run_lattice(Q, rho, u, wparams, steps, warmup, dist, clocks=None, store="fp32", onepass=False):
     import torch
 
     from paper_2306_16274_gb300 import Params, Simulation
-    p = Params(lattice=Q, shape=SHAPE, store=store, **wparams)
+    p = Params(lattice=Q, shape=SHAPE, store=store, onepass=onepass, **wparams)
     stream = torch.cuda.Stream()
     sim = Simulation(p, stream=stream)
     with torch.cuda.stream(stream):
@@ -523,6 +526,7 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=2000)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--no-onepass", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=24)
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
@@ -560,6 +564,9 @@ def main():
     e2e = None if args.no_e2e else run_e2e(19, rho, u, wparams, args.steps, dist, ws)
     f16 = {} if (args.no_fp16 or not single) else {
         Q: run_lattice(Q, rho, u, wparams, args.steps, args.warmup, dist, store="fp16")
+                                   for Q in ((19,) if args.no_q27 else (19, 27))}
+    one = {} if (args.no_onepass or not single) else {
+        Q: run_lattice(Q, rho, u, wparams, args.steps, args.warmup, dist, onepass=True)
                                    for Q in ((19,) if args.no_q27 else (19, 27))}
     batched = None if (args.no_batched or not single or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
     serving = None if (args.no_serving or not single or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
@@ -614,6 +621,18 @@ def main():
                 "collide_gbs": abh["collide"] * n / (cms * 1e-3) / 1e9,
                 "psi_gbs": abh["psi"] * n / (pms * 1e-3) / 1e9, "mass_drift_rel": r["mass_drift"],
                 "device_bytes": r["device_bytes"]}
+    if one:
+        line["onepass"] = {"note": "one pass per step over two population copies (same results bit for bit, "
+                                   "tests/test_gpu_onepass.py); twice the population memory"}
+        for Q, r in one.items():
+            ab1 = algorithmic_bytes(Q, onepass=True)
+            cms = r["kernel_ms"]["collide"] / max(r["kernel_launches"]["collide"], 1)
+            line["onepass"][f"d3q{Q}"] = {
+                "value": r["mlups_local"], "unit": UNIT, "ms_per_step": r["ms"] / args.steps,
+                "bytes_per_cell": ab1["step"],
+                "hbm_frac_step": ab1["step"] * n * args.steps / (r["ms"] * 1e-3) / 1e9 / peak,
+                "kernel_gbs": ab1["collide"] * n / (cms * 1e-3) / 1e9, "kernel_avg_ms": cms,
+                "mass_drift_rel": r["mass_drift"], "device_bytes": r["device_bytes"]}
     if batched:
         line["batched"] = batched
     if serving:

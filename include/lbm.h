@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 2
+#define LBM_ABI_VERSION 3
 
 /* Largest nx, ny or nz: the density/psi pass launches one block row per z plane. */
 #define LBM_MAX_EXTENT 65535
@@ -106,9 +106,11 @@ typedef struct {
     double nu_l, nu_v;      /* (Sec. IV A) replaces s2 per cell; 0: s2 is used everywhere    */
     double rho_l, rho_v;
     double g[3];            /* body force per unit mass (F includes rho g)                   */
-    double psi_fp64_rho;    /* C-S only: cells with rho >= this evaluate p_EOS - rho c_s^2   */
-                            /* in FP64 (liquid branch); a negative value selects the default */
-                            /* b * rho_c = 0.52177 (critical density); +inf: never           */
+    double psi_ext_rho;     /* C-S only: cells with rho >= this evaluate p_EOS - rho c_s^2   */
+                            /* in float-float arithmetic (~44 bits; the liquid branch, where */
+                            /* the two terms of p_EOS nearly cancel); a negative value       */
+                            /* selects the default b * rho_c = 0.52177 (critical density);   */
+                            /* +inf: never                                                   */
     int32_t zchunk;         /* tuning: z planes one collide block marches through; 0 = chosen */
                             /* from the domain size (results do not depend on it)            */
     int32_t store;          /* LBM_STORE_FP32 (default) or LBM_STORE_FP16.  The paper stores */
@@ -116,11 +118,17 @@ typedef struct {
                             /* its error against the FP64 oracle is reported per result.     */
                             /* FP16 contexts step with the whole-grid kernels and cannot     */
                             /* join a batch.                                                 */
+    int32_t onepass;        /* 1: one pass per step over two population copies (read one,    */
+                            /* write the other, pull streaming): the collide pass computes   */
+                            /* rho and psi of each tile and a one-cell halo itself, so no    */
+                            /* separate density/psi pass and no psi field are needed; same   */
+                            /* results bit for bit, twice the population memory.  Periodic  */
+                            /* boundaries, no solid mask, FP32 store; cannot join a batch.   */
 } lbm_params;
 
 /* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,
  * s0 = s1 = 1, s2b = s3b = 0.6, others 1.2 (text after Eq. e12), sigma = 0.1
- * (Sec. III A), everything else 0, psi_fp64_rho = -1 (default threshold),
+ * (Sec. III A), everything else 0, psi_ext_rho = -1 (default threshold),
  * zchunk = 0 (automatic). */
 void lbm_default_params(lbm_params* p);
 

@@ -64,6 +64,7 @@ KParams physics_of(const KParams& k) {
     p.wall_x = p.wall_y = p.wall_z = 0;
     p.plane = p.ncell = 0;
     for (float*& q : p.fq) q = nullptr;
+    for (float*& q : p.gq) q = nullptr;
     p.zchunk = 0;
     return p;
 }
@@ -435,6 +436,8 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, 
         if (!ctxs[i]->initialised) return bfail(nullptr, LBM_ERR_STATE, "every context must be initialised");
         if (ctxs[i]->f16)
             return bfail(nullptr, LBM_ERR_ARG, "contexts with the FP16 store cannot join a batch");
+        if (ctxs[i]->onepass)
+            return bfail(nullptr, LBM_ERR_ARG, "contexts with the one-pass layout cannot join a batch");
         if (ctxs[i]->parity != ctxs[0]->parity)
             return bfail(nullptr, LBM_ERR_STATE, "all contexts must have taken an equal number of steps mod 2");
         for (int j = 0; j < i; ++j)

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -68,6 +69,12 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         why = "store must be LBM_STORE_FP32 or LBM_STORE_FP16";
         return LBM_ERR_ARG;
     }
+    if (p->onepass != 0 && p->onepass != 1) { why = "onepass must be 0 or 1"; return LBM_ERR_ARG; }
+    if (p->onepass && (p->store != LBM_STORE_FP32 || p->bc[0] != LBM_BC_PERIODIC || p->bc[1] != LBM_BC_PERIODIC ||
+                       p->bc[2] != LBM_BC_PERIODIC)) {
+        why = "onepass needs the FP32 store and periodic boundaries on all axes";
+        return LBM_ERR_ARG;
+    }
     if (p->variable_nu) {
         if (!(p->rho_l != p->rho_v) || !(p->nu_l > 0.0) || !(p->nu_v > 0.0)) {
             why = "variable viscosity needs rho_l != rho_v and nu_l, nu_v > 0";
@@ -75,6 +82,12 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         }
     }
     return LBM_OK;
+}
+
+// d as an unevaluated float pair: hi = d rounded to float, lo = the remainder rounded to float
+float2 ff_split(double d) {
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
 }
 
 KParams derive(const lbm_params& p, long long plane) {
@@ -91,17 +104,18 @@ KParams derive(const lbm_params& p, long long plane) {
     k.eos = p.eos;
     if (p.eos == LBM_EOS_CS) {
         const double a = p.eos_p[0], b = p.eos_p[1], R = p.eos_p[2], T = p.eos_p[3];
-        k.cs_a_d = a;
-        k.cs_b4_d = b / 4.0;
-        k.cs_RT_d = R * T;
+        k.cs_a_ff = ff_split(a);
+        k.cs_b4_ff = ff_split(b / 4.0);
+        k.cs_RT_ff = ff_split(R * T);
+        k.third_ff = ff_split(1.0 / 3.0);
         k.cs_a = (float)a;
         k.cs_b4 = (float)(b / 4.0);
         k.cs_RT = (float)(R * T);
-        // default FP64 threshold: the critical density b rho_c = 0.52177 of the C-S fluid
-        const double thr = p.psi_fp64_rho < 0.0 ? 0.52177 / b : p.psi_fp64_rho;
-        k.psi_fp64_rho = (float)thr;
+        // default threshold of the float-float branch: the critical density b rho_c = 0.52177
+        const double thr = p.psi_ext_rho < 0.0 ? 0.52177 / b : p.psi_ext_rho;
+        k.psi_ext_rho = (float)thr;
     } else {
-        k.psi_fp64_rho = INFINITY;
+        k.psi_ext_rho = INFINITY;
     }
     if (p.eos == LBM_EOS_PIECEWISE) {
         k.pw_rho1 = (float)p.eos_p[0];
@@ -116,8 +130,9 @@ KParams derive(const lbm_params& p, long long plane) {
     const double G = k.multiphase ? p.G : 0.0;
     k.G = (float)G;
     k.G_ads = k.multiphase ? (float)p.G_ads : 0.0f;
-    k.two_over_G_d = G != 0.0 ? 2.0 / G : 0.0;
-    k.two_over_G = (float)k.two_over_G_d;
+    const double tg = G != 0.0 ? 2.0 / G : 0.0;
+    k.two_over_G_ff = ff_split(tg);
+    k.two_over_G = (float)tg;
     k.kappa_G_half = (float)(p.kappa * G / 2.0);
     const double t_e = 1.0 / p.s[3] - 0.5;    // s_e = s2b (rate of m_7)
     k.sigma_coef = (float)(k.multiphase ? 6.0 * p.sigma * G * G / t_e : 0.0);
@@ -167,6 +182,15 @@ cudaError_t run_psi(lbm_ctx* c) {
                       : lbm::launch_psi_q27(c->kp, c->parity, s, bufs(c), c->stream);
 }
 
+// one-pass layout: one launch per step, then the copies trade places
+cudaError_t run_onepass(lbm_ctx* c) {
+    cudaError_t e = c->Q == 19 ? lbm::launch_onepass_q19(c->kp, c->status, c->stream)
+                               : lbm::launch_onepass_q27(c->kp, c->status, c->stream);
+    std::swap(c->f, c->f2);
+    for (int i = 0; i < 27; ++i) std::swap(c->kp.fq[i], c->kp.gq[i]);
+    return e;
+}
+
 cudaError_t run_collide(lbm_ctx* c) {
     const int s = has_solids(c);
     cudaError_t e = c->Q == 19 ? lbm::launch_collide_q19(c->kp, c->parity, s, bufs(c), c->stream)
@@ -198,7 +222,7 @@ cudaError_t drain_timing(lbm_ctx* c) {
         c->ms[1] += a;   // collide runs first in a step
         c->ms[0] += b;
         c->launches[1] += 1;
-        if (c->kp.multiphase || c->f16) c->launches[0] += 1;
+        if ((c->kp.multiphase || c->f16) && !c->onepass) c->launches[0] += 1;
     }
     c->ev_used = 0;
     return cudaSuccess;
@@ -244,9 +268,9 @@ cudaError_t ensure_staging(lbm_ctx* c, size_t floats) {
 }
 
 // Device bytes a context holds once initialised (host staging excluded).
-size_t resident_bytes(const KParams& k, int Q, bool f16, bool with_solid) {
+size_t resident_bytes(const KParams& k, int Q, bool f16, bool with_solid, bool onepass) {
     const size_t n = (size_t)k.ncell;
-    size_t b = (size_t)Q * (size_t)k.plane * (f16 ? 2 : sizeof(float));   // populations
+    size_t b = (size_t)Q * (size_t)k.plane * (f16 ? 2 : sizeof(float)) * (onepass ? 2 : 1);   // populations
     if (f16) b += 2 * n * sizeof(float);                                   // two density fields
     b += n * sizeof(float);                                   // psi
     b += 64;                                                  // status word
@@ -274,7 +298,7 @@ void lbm_default_params(lbm_params* p) {
     p->sigma = 0.1;
     const double s[10] = {1.0, 1.0, 1.2, 0.6, 1.2, 0.6, 1.2, 1.2, 1.2, 1.2};
     for (int i = 0; i < 10; ++i) p->s[i] = s[i];
-    p->psi_fp64_rho = -1.0;
+    p->psi_ext_rho = -1.0;
 }
 
 lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out) {
@@ -304,6 +328,12 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         for (int i = 0; i < c->Q; ++i)
             c->kp.fq[i] = reinterpret_cast<float*>(reinterpret_cast<char*>(c->f) + (size_t)i * plane * esize);
     for (int k = 0; k < 2 && c->f16 && e == cudaSuccess; ++k) e = alloc((void**)&c->rbuf[k], (size_t)n * sizeof(float));
+    c->onepass = params->onepass;
+    if (c->onepass && e == cudaSuccess) {
+        e = alloc((void**)&c->f2, (size_t)c->Q * plane * sizeof(float));
+        if (e == cudaSuccess)
+            for (int i = 0; i < c->Q; ++i) c->kp.gq[i] = c->f2 + (size_t)i * plane;
+    }
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
@@ -334,6 +364,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         d_rho = c->staging;
         d_u = c->staging + n;
     }
+    if (solid && c->onepass) return fail(c, LBM_ERR_ARG, "onepass contexts take no solid mask");
     if (solid) {
         if (!c->nbmask) {
             CK(c, cudaMalloc((void**)&c->nbmask, n * sizeof(uint32_t)));
@@ -353,6 +384,25 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->nbmask = nullptr;
     }
     c->tile_flags.clear();
+    if (c->onepass) {
+        // natural-order populations into the other copy, then shifted into the pull layout
+        lbm::KParams kn = c->kp;
+        for (int i = 0; i < 27; ++i) kn.fq[i] = c->kp.gq[i];
+        lbm::Bufs bn = bufs(c);
+        bn.f = c->f2;
+        CK(c, c->Q == 19 ? lbm::launch_init_q19(kn, bn, d_rho, d_u, c->stream)
+                         : lbm::launch_init_q27(kn, bn, d_rho, d_u, c->stream));
+        CK(c, c->Q == 19 ? lbm::launch_pull_store_q19(c->kp, c->f2, c->kp.plane, c->f, c->stream)
+                         : lbm::launch_pull_store_q27(c->kp, c->f2, c->kp.plane, c->f, c->stream));
+        c->parity = 2;
+        c->t = 0;
+        c->sticky = LBM_OK;
+        CK(c, cudaMemsetAsync(c->status, 0, 64, c->stream));
+        CK(c, run_psi(c));
+        c->initialised = true;
+        if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
     CK(c, c->Q == 19 ? lbm::launch_init_q19(c->kp, bufs(c), d_rho, d_u, c->stream)
                      : lbm::launch_init_q27(c->kp, bufs(c), d_rho, d_u, c->stream));
     c->parity = 0;
@@ -370,6 +420,16 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
     if (n < 0) return fail(c, LBM_ERR_ARG, "n must be >= 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields");
     if (c->sticky != LBM_OK) return c->sticky;
+    if (c->onepass) {
+        for (int32_t k = 0; k < n; ++k) {
+            if (c->timing) CK(c, record(c));
+            CK(c, run_onepass(c));
+            if (c->timing) CK(c, record(c));
+            if (c->timing) CK(c, record(c));
+            c->t += 1;
+        }
+        return LBM_OK;
+    }
     if (has_solids(c) && !c->timing && !c->f16 && n > 0 &&
         (unsigned long long)c->Q * (unsigned long long)c->kp.plane <= 0xFFFFFFFFull) {
         // walls or solids: the tile path, which runs solid-free tiles without solid handling
@@ -409,6 +469,7 @@ lbm_status lbm_get_moments(lbm_ctx* c, float* rho, float* u, double* sums, int o
     float* d_u = on_device ? u : (u ? c->staging + n : nullptr);
     int nb = 0;
     const int s = has_solids(c);
+    if (c->onepass) CK(c, run_psi(c));   // the one-pass step keeps no psi field
     CK(c, c->Q == 19 ? lbm::launch_moments_q19(c->kp, c->parity, s, bufs(c), d_rho, d_u, c->partials, &nb, c->stream)
                      : lbm::launch_moments_q27(c->kp, c->parity, s, bufs(c), d_rho, d_u, c->partials, &nb, c->stream));
     CK(c, lbm::launch_finish_sums(c->partials, nb, c->sums, c->stream));
@@ -423,6 +484,7 @@ lbm_status lbm_get_moments(lbm_ctx* c, float* rho, float* u, double* sums, int o
 lbm_status lbm_get_psi(lbm_ctx* c, float* psi, int on_device) {
     if (!c || !psi) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_get_psi before lbm_init_fields");
+    if (c->onepass) CK(c, run_psi(c));
     lbm_status s = copy_out(c, psi, c->psi, c->kp.ncell * sizeof(float), on_device);
     if (s != LBM_OK) return s;
     CK(c, cudaStreamSynchronize(c->stream));
@@ -446,6 +508,24 @@ lbm_status lbm_get_populations(lbm_ctx* c, float* f, int on_device) {
 lbm_status lbm_set_populations(lbm_ctx* c, const float* f, int on_device) {
     if (!c || !f) return LBM_ERR_ARG;
     const long long n = c->kp.ncell;
+    if (c->onepass) {
+        const float* d_f = f;
+        if (!on_device) {
+            CK(c, ensure_staging(c, (size_t)c->Q * n));
+            CK(c, cudaMemcpyAsync(c->staging, f, (size_t)c->Q * n * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream));
+            d_f = c->staging;
+        }
+        CK(c, c->Q == 19 ? lbm::launch_pull_store_q19(c->kp, d_f, n, c->f, c->stream)
+                         : lbm::launch_pull_store_q27(c->kp, d_f, n, c->f, c->stream));
+        c->parity = 2;
+        c->sticky = LBM_OK;
+        CK(c, cudaMemsetAsync(c->status, 0, 64, c->stream));
+        CK(c, run_psi(c));
+        c->initialised = true;
+        CK(c, cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
     if (c->f16) {
         // densities of the given state, then the slots relative to them
         const float* d_f = f;
@@ -509,7 +589,8 @@ lbm_status lbm_estimate_bytes(const lbm_params* params, int32_t with_solid, size
     if (v != LBM_OK) return fail(nullptr, v, why);
     const long long n = (long long)params->nx * params->ny * params->nz;
     const KParams k = derive(*params, (n + 63) / 64 * 64);
-    *bytes = resident_bytes(k, params->lattice, params->store == LBM_STORE_FP16, with_solid != 0);
+    *bytes = resident_bytes(k, params->lattice, params->store == LBM_STORE_FP16, with_solid != 0,
+                            params->onepass != 0);
     return LBM_OK;
 }
 
@@ -536,7 +617,7 @@ void lbm_destroy(lbm_ctx* c) {
     if (c->stream || c->f) (void)cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->ev) (void)cudaEventDestroy(e);
     void* ptrs[] = {c->f, c->psi, c->nbmask, c->status, c->partials, c->sums, c->staging, c->solid_dev,
-                    c->rbuf[0], c->rbuf[1]};
+                    c->rbuf[0], c->rbuf[1], c->f2};
     for (void* p : ptrs)
         if (p) (void)cudaFree(p);
     delete c;

@@ -17,6 +17,8 @@ struct lbm_ctx {
     // device state
     float* f = nullptr;          // Q planes of `plane` slots (AA layout): floats, or __half with f16
     int f16 = 0;                 // shifted FP16 store (LBM_STORE_FP16)
+    int onepass = 0;             // one-pass layout: f is the copy being read, f2 the one written
+    float* f2 = nullptr;
     float* rbuf[2] = {nullptr, nullptr};   // f16: density fields, see bufs() in capi.cu
     int rs = 0;
     float* psi = nullptr;        // ncell floats

@@ -1,6 +1,7 @@
 // Kernels of one lattice; included by kernels_q19.cu / kernels_q27.cu with LBM_Q set.
 #pragma once
 
+#include <cmath>
 #include <type_traits>
 
 #include "lbm_device.cuh"
@@ -245,6 +246,122 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     collide_tile<PARITY, SOLIDS, MULTIPHASE, F16>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
                                                   blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring, ring + 4,
                                                   rsrc, rown);
+}
+
+// ---- one-pass update with two population copies (periodic domains without solids, FP32).
+// kp.fq holds the copy being read (pull layout: population i of x is slot i of x - e_i, written by
+// x - e_i in the previous step), kp.gq the copy this step writes (slot i of x = f*_i(x)).  Nothing
+// writes kp.fq during the launch, so a block can pull the populations of cells it does not own:
+// it computes rho and psi of its tile and of a one-cell halo itself, one plane ahead of the
+// collision, with the same summation order and EOS code as the density/psi pass.  The step reads
+// and writes each population once and needs no psi field.
+__device__ __forceinline__ void pull_offsets(Off32& o, int x, int y, int nx, int ny) {
+    o.xo[0] = (uint32_t)wrap1(x - 1, nx);
+    o.xo[1] = (uint32_t)x;
+    o.xo[2] = (uint32_t)wrap1(x + 1, nx);
+    o.yo[0] = (uint32_t)wrap1(y - 1, ny) * (uint32_t)nx;
+    o.yo[1] = (uint32_t)y * (uint32_t)nx;
+    o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
+}
+
+// Tiles of 32 x BY cells; the ring plane is (32 + 2) x (BY + 2) with a border of 2 (32 + 2) + 2 BY
+// cells, whose densities the first threads of the block compute besides their own.
+template <bool MULTIPHASE, int BY, int MINB>
+__global__ void __launch_bounds__(32 * BY, MINB) collide_onepass_kernel(const KParams kp, unsigned* status,
+                                                                        int zchunk) {
+    constexpr int RX = 34, RY = BY + 2, RP = RX * RY, HALO = 2 * RX + 2 * BY;
+    static_assert(HALO <= 32 * BY, "one border cell per thread at most");
+    __shared__ float ring[4][RP];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * BY, z0 = blockIdx.z * zchunk;
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    const int zend = min(z0 + zchunk, nz);
+    const PlanePtrs rd{kp};
+
+    // this thread's ring cell (its own cell, wrapped where the tile overhangs the domain)
+    Off32 o;
+    pull_offsets(o, x % nx, y % ny, nx, ny);
+    const int lc = (ty + 1) * RX + tx + 1;
+    // and, for the first HALO threads, one border cell of the ring plane
+    Off32 oh;
+    int hl = 0;
+    if (MULTIPHASE && tid < HALO) {
+        int rx, ry;
+        if (tid < RX) { rx = tid; ry = 0; }
+        else if (tid < 2 * RX) { rx = tid - RX; ry = RY - 1; }
+        else if (tid < 2 * RX + BY) { rx = 0; ry = 1 + tid - 2 * RX; }
+        else { rx = RX - 1; ry = 1 + tid - 2 * RX - BY; }
+        hl = ry * RX + rx;
+        pull_offsets(oh, (x0 - 1 + rx + nx) % nx, (y0 - 1 + ry + ny) % ny, nx, ny);
+    }
+
+    // psi of plane zz at this thread's ring cells; the own cell's populations are returned in p
+    auto plane_psi = [&](float* slot, int zz, float (&p)[Q]) {
+        zz = wrap1(zz, nz);
+        set_plane(o, zz, nz, nxy);
+        gather32<Q, 2, false>(rd, o, 0u, p);
+        if (MULTIPHASE) {
+            float rho = 0.0f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rho += p[i];
+            slot[lc] = eval_psi(kp, rho, status);
+            if (tid < HALO) {
+                set_plane(oh, zz, nz, nxy);
+                float q[Q];
+                gather32<Q, 2, false>(rd, oh, 0u, q);
+                float rh = 0.0f;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) rh += q[i];
+                slot[hl] = eval_psi(kp, rh, status);
+            }
+        }
+    };
+
+    float pn[Q];
+    if (MULTIPHASE) {
+        float tmp[Q];
+        plane_psi(ring[0], z0 - 1, tmp);
+    }
+    plane_psi(ring[1], z0, pn);
+    for (int z = z0, j = 0; z < zend; ++z, ++j) {
+        float p[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) p[i] = pn[i];
+        if (MULTIPHASE || z + 1 < zend) plane_psi(ring[(j + 2) & 3], z + 1, pn);
+        if (MULTIPHASE) __syncthreads();
+        if (!act) continue;
+        set_plane(o, z, nz, nxy);
+        Forces Fo;
+        if (MULTIPHASE) {
+            Fo = stencil_forces3<Q, false>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
+                                           RX, 0u);
+        } else {
+            Fo.fx = Fo.fy = Fo.fz = 0.f;
+            Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+            Fo.s2 = 0.f;
+        }
+        float rho, ux, uy, uz;
+        collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+        if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) kp.gq[i][o.c] = p[i];
+    }
+}
+
+// natural-order populations (plane i at fin + i * fstride) -> one-pass layout (slot i of x - e_i)
+__global__ void pull_store_kernel(KParams kp, const float* __restrict__ fin, long long fstride,
+                                  float* __restrict__ fout) {
+    const long long n = kp.ncell;
+    const long long nxy = (long long)kp.nx * kp.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const Cell c = make_cell(kp, (int)(idx % kp.nx), (int)((idx / kp.nx) % kp.ny), (int)(idx / nxy));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fout[i * kp.plane + idx] = fin[i * fstride + c.nb(EX(i), EY(i), EZ(i))];
+    }
 }
 
 // multi-domain collide-stream pass: one block per tile of any member of the launch's table;
@@ -572,7 +689,8 @@ cudaError_t launch_collide_store(dim3 g, dim3 b, cudaStream_t st, const KParams&
 
 template <bool F16>
 void launch_psi_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int parity, int solids, const Bufs& B) {
-    if (parity == 0 && !solids) psi_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+    if (parity == 2) psi_kernel<2, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
+    else if (parity == 0 && !solids) psi_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
     else if (parity == 0) psi_kernel<0, true, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
     else if (!solids) psi_kernel<1, false, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
     else psi_kernel<1, true, F16><<<g, b, 0, st>>>(kp, B.psi, B.nbmask, B.status, B.rsrc, B.rnew);
@@ -596,7 +714,8 @@ void launch_moments_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, in
 template <bool F16>
 void launch_gather_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int parity, int solids, const Bufs& B,
                          float* out) {
-    if (parity == 0 && !solids) gather_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
+    if (parity == 2) gather_kernel<2, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
+    else if (parity == 0 && !solids) gather_kernel<0, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
     else if (parity == 0) gather_kernel<0, true, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
     else if (!solids) gather_kernel<1, false, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
     else gather_kernel<1, true, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
@@ -615,15 +734,43 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
 }
 
 // z planes per block: enough blocks for a few waves of resident blocks on 152 SMs
-static int collide_zchunk(const KParams& kp) {
+// z-planes per block of the z-marching kernels.  Blocks of equal size run in waves of
+// (SMs x resident blocks); a last wave that is mostly empty leaves SMs idle, and every chunk
+// costs about h planes' worth of extra time at its start (the psi planes below and at its first
+// plane, the first loads with nothing to overlap them).  Over the chunk counts that give at
+// least three waves, the choice minimises (1 + h / zc) x ceil(waves) / waves.
+static int choose_zchunk(const KParams& kp, double h) {
     if (kp.zchunk > 0) return kp.zchunk < kp.nz ? kp.zchunk : kp.nz;
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || n <= 0)
+            n = 152;
+        return n;
+    }();
+    thread_local long long key[4] = {-1, -1, -1, -1};
+    thread_local int cached = 1;
+    const long long k[4] = {kp.nx, kp.ny, kp.nz, (long long)(h * 1024.0)};
+    if (k[0] == key[0] && k[1] == key[1] && k[2] == key[2] && k[3] == key[3]) return cached;
+    const double cap = (double)sms * ZM_MINB;
     const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + ZM_BY - 1) / ZM_BY);
-    const long long target = 152LL * ZM_MINB * 4;
-    long long chunks = (target + cols - 1) / cols;
-    if (chunks > kp.nz) chunks = kp.nz;
-    if (chunks < 1) chunks = 1;
-    return (int)((kp.nz + chunks - 1) / chunks);
+    int best = kp.nz;
+    double best_cost = 1e300;
+    for (int c = 1; c <= kp.nz; ++c) {
+        const int zc = (kp.nz + c - 1) / c;
+        const int chunks = (kp.nz + zc - 1) / zc;
+        if (chunks != c) continue;                 // the same split as a smaller count
+        const double waves = (double)(cols * chunks) / cap;
+        if (waves < 3.0 && c < kp.nz) continue;
+        const double cost = (1.0 + h / zc) * std::ceil(waves) / waves;
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = zc; }
+    }
+    for (int i = 0; i < 4; ++i) key[i] = k[i];
+    cached = best;
+    return best;
 }
+
+static int collide_zchunk(const KParams& kp) { return choose_zchunk(kp, 1.0); }
 
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B,
                                              cudaStream_t st) {
@@ -678,6 +825,23 @@ cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, cons
     return cudaGetLastError();
 }
 
+cudaError_t LBM_CAT(launch_onepass_q, LBM_Q)(const KParams& kp, unsigned* status, cudaStream_t st) {
+    // a chunk starts with two psi planes whose loads nothing overlaps
+    const int zc = choose_zchunk(kp, 1.5);
+    const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
+    if (kp.multiphase) collide_onepass_kernel<true, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);
+    else collide_onepass_kernel<false, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_pull_store_q, LBM_Q)(const KParams& kp, const float* fin, long long fstride, float* fout,
+                                                cudaStream_t st) {
+    const long long blocks = (kp.ncell + 255) / 256;
+    const int g = (int)(blocks < 152LL * 64 ? blocks : 152LL * 64);
+    pull_store_kernel<<<g, 256, 0, st>>>(kp, fin, fstride, fout);
+    return cudaGetLastError();
+}
+
 int LBM_CAT(tile_height_q, LBM_Q)() { return ZM_BY; }
 int LBM_CAT(resident_blocks_q, LBM_Q)() { return ZM_MINB; }
 
@@ -705,6 +869,13 @@ cudaError_t LBM_CAT(launch_moments_q, LBM_Q)(const KParams& kp, int parity, int 
                                              float* u, double* partials, int* nblocks, cudaStream_t st) {
     const dim3 g = cs_grid(kp), b(CS_BX, CS_BY, CS_BZ);
     *nblocks = (int)(g.x * g.y * g.z);
+    if (parity == 2) {   // one-pass layout (FP32, no solids)
+        if (kp.multiphase)
+            moments_kernel<2, false, true, false><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, nullptr);
+        else
+            moments_kernel<2, false, false, false><<<g, b, 0, st>>>(kp, B.f, B.psi, B.nbmask, rho, u, partials, nullptr);
+        return cudaGetLastError();
+    }
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
     if (B.f16) launch_moments_store<true>(g, b, st, kp, key, B, rho, u, partials);
     else launch_moments_store<false>(g, b, st, kp, key, B, rho, u, partials);

@@ -12,6 +12,10 @@
 // neighbour reads/writes the cell's own slot instead (f_i(x) <- slot i of x,
 // f*_i -> slot ibar of x); an even step is local and needs no test.
 //
+// One-pass layout (optional, PARITY == 2 below): two copies; the copy being read holds the
+// post-collision values of the previous step where they were computed, so population i of x is
+// slot i of x - e_i (pull), and the step writes slot i of x in the other copy.
+//
 // Shifted FP16 store (optional): a slot holds h = f / rho_w - omega_i in half precision,
 // rho_w being the density of the cell that wrote it, kept in FP32 in a density field.  The
 // population f_i arriving at x was written by x - e_i (by x itself where that neighbour is
@@ -142,7 +146,9 @@ __device__ __forceinline__ void gather(const KParams& kp, const T* __restrict__ 
                                        float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (PARITY == 0 || i == 0) {
+        if (PARITY == 2) {   // one-pass layout: pull from x - e_i
+            p[i] = ldpop(f + i * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
+        } else if (PARITY == 0 || i == 0) {
             p[i] = ldpop(f + i * kp.plane + c.idx);
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
             p[i] = ldpop(f + i * kp.plane + c.idx);   // reflected at the wall in the previous step
@@ -189,18 +195,72 @@ struct RsCell {
 };
 
 // ------------------------------------------------------------------ equation of state -> psi
-// psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. II C).  The Carnahan-Starling
-// liquid branch (rho >= psi_fp64_rho) is evaluated in FP64.
+// ---- float-float arithmetic: a value is the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, from the error-free transformations of Dekker (1971) and Knuth (TwoSum).
+// The _rn intrinsics keep the compiler from fusing the error terms into other operations.
+struct FF {
+    float hi, lo;
+};
+// a + b exactly, given |a| >= |b| (or a = 0)
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a + b exactly, any magnitudes
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.hi, y.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_one_plus(FF x) {
+    const FF s = ff_two_sum(1.0f, x.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+// products: the rounding error of hi * hi is exact with one FMA
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, __fmaf_rn(x.hi, y.hi, -p)));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_mul(FF x, float f) {
+    const float p = __fmul_rn(x.hi, f);
+    return ff_fast_two_sum(p, __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p)));
+}
+// x / y: a first quotient, then the exact remainder's quotient as its correction
+__device__ __forceinline__ FF ff_div(FF x, FF y) {
+    const float r = __frcp_rn(y.hi);
+    const float q1 = __fmul_rn(x.hi, r);
+    const FF rem = ff_add(x, ff_neg(ff_mul(y, q1)));
+    return ff_fast_two_sum(q1, __fmul_rn(rem.hi, r));
+}
+__device__ __forceinline__ FF ff_of(float2 v) { return FF{v.x, v.y}; }
+
+// (2/G)(p_EOS - rho c_s^2) of the Carnahan-Starling EOS in float-float.  On the liquid side the
+// two terms of p_EOS nearly cancel (rho RT g(eta) ~ a rho^2 at coexistence), so a plain FP32
+// evaluation keeps only ~14 good bits of p_EOS; here the result is ~44 bits good before it is
+// rounded to float (written as rho (RT g(eta) / (1 - eta)^3 - a rho) - rho / 3, the same function).
+__device__ __forceinline__ float cs_psi2_ff(const KParams& kp, float rho) {
+    const FF eta = ff_mul(ff_of(kp.cs_b4_ff), rho);
+    const FF om = ff_one_plus(ff_neg(eta));                                  // 1 - eta
+    const FF om3 = ff_mul(ff_mul(om, om), om);
+    const FF g = ff_one_plus(ff_mul(eta, ff_one_plus(ff_mul(eta, om))));    // 1 + eta + eta^2 - eta^3
+    const FF br = ff_add(ff_div(ff_mul(ff_of(kp.cs_RT_ff), g), om3), ff_neg(ff_mul(ff_of(kp.cs_a_ff), rho)));
+    const FF d = ff_add(ff_mul(br, rho), ff_neg(ff_mul(ff_of(kp.third_ff), rho)));
+    return ff_mul(ff_of(kp.two_over_G_ff), d).hi;
+}
+
+// psi = sqrt(2 (p_EOS - rho c_s^2) / G) (Sec. II C).  The Carnahan-Starling liquid branch
+// (rho >= psi_ext_rho) is evaluated in float-float arithmetic.
 __device__ __forceinline__ float eval_psi(const KParams& kp, float rho, unsigned* status) {
     float psi2;
     if (kp.eos == 1) {
-        if (rho >= kp.psi_fp64_rho) {
-            const double r = rho;
-            const double eta = kp.cs_b4_d * r;
-            const double om = 1.0 - eta;
-            const double p = r * kp.cs_RT_d * (1.0 + eta * (1.0 + eta * (1.0 - eta))) / (om * om * om) -
-                             kp.cs_a_d * r * r;
-            psi2 = (float)(kp.two_over_G_d * (p - r * (1.0 / 3.0)));
+        if (rho >= kp.psi_ext_rho) {
+            psi2 = cs_psi2_ff(kp, rho);
         } else {
             const float eta = kp.cs_b4 * rho;
             const float om = 1.0f - eta;
@@ -424,7 +484,9 @@ template <int Q, int PARITY, bool SOLIDS, class A>
 __device__ __forceinline__ void gather32(const A& a, const Off32& o, uint32_t bits, float (&p)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (PARITY == 0 || i == 0) {
+        if (PARITY == 2) {   // one-pass layout: pull from x - e_i
+            p[i] = ldpop(a.ptr(i, o.nb(-EX(i), -EY(i), -EZ(i))));
+        } else if (PARITY == 0 || i == 0) {
             p[i] = ldpop(a.ptr(i, o.c));
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
             p[i] = ldpop(a.ptr(i, o.c));

@@ -21,12 +21,13 @@ struct KParams {
     int eos;                      // 1 Carnahan-Starling, 2 piecewise linear
     // Carnahan-Starling: p = rho RT g(eta) - a rho^2, eta = (b/4) rho
     float cs_a, cs_b4, cs_RT;
-    double cs_a_d, cs_b4_d, cs_RT_d;
-    float psi_fp64_rho;           // rho >= this: evaluate the EOS and p - rho c_s^2 in FP64
+    float2 cs_a_ff, cs_b4_ff, cs_RT_ff;   // the same as float-float pairs (hi, lo)
+    float2 third_ff;              // 1/3 = c_s^2 as a float-float pair
+    float psi_ext_rho;            // rho >= this: evaluate the EOS and p - rho c_s^2 in float-float
     // piecewise linear (Eq. e19)
     float pw_rho1, pw_rho2, pw_tv, pw_tm, pw_tl, pw_p1, pw_p2;
     float two_over_G;             // psi^2 = (2/G)(p_EOS - rho c_s^2)
-    double two_over_G_d;
+    float2 two_over_G_ff;
     float G;                      // Eq. e15
     float G_ads;                  // Sec. III E
     float kappa_G_half;           // kappa G / 2 of Eq. e18
@@ -40,6 +41,7 @@ struct KParams {
     float gx, gy, gz;             // body force per unit mass
     float* fq[27];                // base of population plane i (f + i * plane); cells < 2^31
     int zchunk;                   // z planes per collide block (0 = automatic)
+    float* gq[27];                // one-pass layout: planes of the copy the step writes
 };
 
 // Geometry and device buffers of one member of a multi-domain launch (its physics come from the
@@ -103,6 +105,9 @@ struct Bufs {
                                       cudaStream_t st);                                               \
     cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const Bufs& B, float thr, int* out, \
                                     cudaStream_t st);                                               \
+    cudaError_t launch_onepass_q##Q(const KParams& kp, unsigned* status, cudaStream_t st);          \
+    cudaError_t launch_pull_store_q##Q(const KParams& kp, const float* fin, long long fstride,       \
+                                       float* fout, cudaStream_t st);                               \
     int tile_height_q##Q();                                                                         \
     int resident_blocks_q##Q();
 

@@ -37,8 +37,8 @@ class lbm_params(ctypes.Structure):
         ("G", ctypes.c_double), ("G_ads", ctypes.c_double), ("kappa", ctypes.c_double), ("sigma", ctypes.c_double),
         ("s", ctypes.c_double * 10), ("variable_nu", ctypes.c_int32),
         ("nu_l", ctypes.c_double), ("nu_v", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
-        ("g", ctypes.c_double * 3), ("psi_fp64_rho", ctypes.c_double), ("zchunk", ctypes.c_int32),
-        ("store", ctypes.c_int32),
+        ("g", ctypes.c_double * 3), ("psi_ext_rho", ctypes.c_double), ("zchunk", ctypes.c_int32),
+        ("store", ctypes.c_int32), ("onepass", ctypes.c_int32),
     ]
 
 
@@ -97,7 +97,8 @@ class Params:
     """Mirror of lbm_params.  shape = (nx, ny, nz); bc per axis "periodic" / "wall";
     eos "none" / "cs" (eos_p = a, b, R, T) / "piecewise" (rho1, rho2, theta_v, theta_m, theta_l);
     rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library);
-    store "fp32" or "fp16" (shifted FP16 population store)."""
+    store "fp32" or "fp16" (shifted FP16 population store); onepass: one pass per step over two
+    population copies (periodic, no solids, FP32)."""
     lattice: int = 19
     shape: tuple = (32, 32, 32)
     bc: tuple = ("periodic", "periodic", "periodic")
@@ -114,9 +115,10 @@ class Params:
     rho_l: float = 1.0
     rho_v: float = 0.0
     g: tuple = (0.0, 0.0, 0.0)
-    psi_fp64_rho: float = -1.0
+    psi_ext_rho: float = -1.0
     zchunk: int = 0
     store: str = "fp32"
+    onepass: bool = False
 
     def to_c(self):
         c = lbm_params()
@@ -137,9 +139,10 @@ class Params:
         c.nu_l, c.nu_v, c.rho_l, c.rho_v = float(self.nu_l), float(self.nu_v), float(self.rho_l), float(self.rho_v)
         for k in range(3):
             c.g[k] = float(self.g[k])
-        c.psi_fp64_rho = float(self.psi_fp64_rho)
+        c.psi_ext_rho = float(self.psi_ext_rho)
         c.zchunk = int(self.zchunk)
         c.store = STORE[self.store] if isinstance(self.store, str) else int(self.store)
+        c.onepass = 1 if self.onepass else 0
         return c
 
     @property

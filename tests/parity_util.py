@@ -39,8 +39,8 @@ def gpu_params(d):
                   rates=dict(d.get("rates", {})), variable_nu=d.get("variable_nu", False),
                   nu_l=d.get("nu_l", 0.0), nu_v=d.get("nu_v", 0.0), rho_l=d.get("rho_l", 1.0),
                   rho_v=d.get("rho_v", 0.0), g=tuple(d.get("g", (0.0, 0.0, 0.0))),
-                  psi_fp64_rho=d.get("psi_fp64_rho", -1.0), zchunk=d.get("zchunk", 0),
-                  store=d.get("store", "fp32"))
+                  psi_ext_rho=d.get("psi_ext_rho", -1.0), zchunk=d.get("zchunk", 0),
+                  store=d.get("store", "fp32"), onepass=d.get("onepass", False))
 
 
 def run_gpu(d, rho, u, solid=None, steps=0, device=True):

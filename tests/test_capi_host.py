@@ -42,7 +42,7 @@ def test_params_struct_layout_matches_header(lib):
     lib.lbm_default_params(ctypes.byref(p))
     assert p.lattice == 19 and (p.nx, p.ny, p.nz) == (32, 32, 32)
     assert list(p.s) == [1.0, 1.0, 1.2, 0.6, 1.2, 0.6, 1.2, 1.2, 1.2, 1.2]
-    assert p.G == -1.0 and p.sigma == 0.1 and p.psi_fp64_rho == -1.0
+    assert p.G == -1.0 and p.sigma == 0.1 and p.psi_ext_rho == -1.0
 
 
 @pytest.mark.parametrize("change,msg", [
@@ -55,6 +55,8 @@ def test_params_struct_layout_matches_header(lib):
     (dict(variable_nu=True, nu_l=0.01, nu_v=0.01, rho_l=1.0, rho_v=1.0), "variable"),
     (dict(bc=(0, 2, 0)), "bc"),
     (dict(store=2), "store"),
+    (dict(onepass=True, bc=(0, 0, 1)), "onepass"),
+    (dict(onepass=True, store="fp16"), "onepass"),
 ])
 def test_invalid_parameters_are_rejected(lib, change, msg):
     kw = dict(lattice=19, shape=(4, 4, 4))
@@ -128,3 +130,21 @@ def test_estimate_bytes_fp16_store(lib):
     for Q in (19, 27):
         want = Q * plane * 2 + 2 * 4 * n + n * 4 + 64 + blocks * 32 + 32
         assert L.estimate_bytes(L.Params(lattice=Q, shape=(nx, ny, nz), store="fp16")) == want
+
+
+def test_onepass_flag_must_be_0_or_1(lib):
+    c = L.Params(lattice=19, shape=(4, 4, 4)).to_c()
+    c.onepass = 2
+    ctx = ctypes.c_void_p()
+    assert lib.lbm_create(ctypes.byref(c), None, ctypes.byref(ctx)) == 1 and not ctx.value
+    assert b"onepass" in lib.lbm_last_error(None)
+
+
+def test_estimate_bytes_onepass_holds_two_population_copies(lib):
+    nx, ny, nz = 40, 36, 24
+    n = nx * ny * nz
+    plane = (n + 63) // 64 * 64
+    blocks = -(-nx // 32) * -(-ny // 4) * -(-nz // 2)
+    for Q in (19, 27):
+        want = 2 * Q * plane * 4 + n * 4 + 64 + blocks * 32 + 32
+        assert L.estimate_bytes(L.Params(lattice=Q, shape=(nx, ny, nz), onepass=True)) == want

@@ -69,18 +69,39 @@ def test_walls_solids_body_force(Q):
 
 @pytest.mark.parametrize("Q", [19, 27])
 def test_psi_after_init(Q):
-    # psi of Sec. II C on both C-S branches (FP32 vapour side, FP64 liquid side) and for the
+    # psi of Sec. II C on both C-S branches (FP32 vapour side, float-float liquid side) and for the
     # piecewise EOS, element by element
     shape = (34, 10, 6)
     for eos, thr in ((U.cs_eos("T0.5"), -1.0), (U.cs_eos("T0.5"), 0.0), (U.pw_eos(), -1.0)):
         kw, rl, rv = eos
-        d = dict(lattice=Q, shape=shape, psi_fp64_rho=thr, **kw)
+        d = dict(lattice=Q, shape=shape, psi_ext_rho=thr, **kw)
         rho, u = W.droplet(shape, 4.0, rl, rv)
         sim = U.run_gpu(d, rho, u)
         ref = U.run_oracle(d, rho, u)
         psi_o = U.olbm.pseudopotential(U.olbm.density(ref.f, ref.solid), ref.solid, ref.p)
         psi_g = sim.psi().cpu().numpy()
         assert np.abs(psi_g - psi_o).max() < 2e-6 * psi_o.max()
+
+
+@pytest.mark.parametrize("T_key", ["T0.5", "T0.6", "T0.7"])
+def test_psi_liquid_branch_is_faithful(T_key):
+    # the float-float liquid branch against the FP64 EOS: psi within one float ulp on every cell
+    # of a density sweep from the critical density to beyond the liquid coexistence density, where
+    # the two terms of p_EOS cancel.  All mass sits in the rest population, so the kernel's density
+    # is the given float exactly, whatever its summation order.
+    kw, rl, rv = U.cs_eos(T_key)
+    shape = (32, 16, 8)
+    n = int(np.prod(shape))
+    rho = np.linspace(0.52177 / 4.0, 1.15 * rl, n).astype(np.float32)
+    d = dict(lattice=19, shape=shape, **kw)
+    sim = U.run_gpu(d, np.full(shape[::-1], rl), np.zeros((3,) + shape[::-1]))
+    f = np.zeros((19, n), dtype=np.float32)
+    f[0] = rho
+    sim.set_populations(f)
+    psi_g = sim.psi(device=False).reshape(-1)
+    psi_o = U.olbm.pseudopotential(rho.astype(np.float64), np.zeros(n, bool), U.oracle_params(d))
+    ulps = np.abs(psi_g.astype(np.float64) - psi_o) / np.spacing(psi_g)
+    assert ulps.max() <= 1.0, (float(ulps.max()), float(rho[ulps.argmax()]))
 
 
 @pytest.mark.parametrize("Q", [19, 27])
