@@ -109,3 +109,20 @@ def test_onepass_rejects_solids_and_batches():
     other = U.run_gpu(dict(d, onepass=True), rho, u, steps=0)
     with pytest.raises(LBMError):
         Batch([other])
+
+
+def test_onepass_status_words():
+    # the one pass evaluates the EOS itself: a density beyond the C-S range and a NaN density are
+    # reported through the same status words as in the two-pass step
+    from paper_2306_16274_gb300 import LBMError
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=19, shape=(8, 8, 8), sigma=0.1, onepass=True, **kw)
+    with pytest.raises(LBMError) as e:
+        U.run_gpu(d, np.full((8, 8, 8), 0.75), np.zeros((3, 8, 8, 8)), steps=1).sync()
+    assert e.value.status == 5
+    rho = np.full((8, 8, 8), 0.2)
+    rho[3, 3, 3] = np.nan
+    sim = U.run_gpu(dict(lattice=27, shape=(8, 8, 8), onepass=True), rho, np.zeros((3, 8, 8, 8)), steps=2)
+    with pytest.raises(LBMError) as e:
+        sim.sync()
+    assert e.value.status == 4
