@@ -40,6 +40,9 @@ WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves th
             "sigma=0.1, G=-1, the paper's default rates, FP32 populations (AA in place)")
 
 
+NOMINAL_HBM_GBS = 8000.0   # HBM3e data-sheet bandwidth, for context beside the measured copy peak
+
+
 def algorithmic_bytes(Q, store="fp32", onepass=False):
     """Bytes per cell update that the method must move: collide-stream reads and writes the Q
     populations and reads psi once (8Q + 4); the density/psi pass reads the Q populations and
@@ -590,7 +593,8 @@ def main():
         "roofline": {"kernel": "collide_kernel (fused collide-stream, D3Q19)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_cell": ab["collide"], "avg_launch_ms": coll_ms},
+                     "algorithmic_bytes_per_cell": ab["collide"], "avg_launch_ms": coll_ms,
+                     "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "kernels": {"collide": {"avg_ms": coll_ms, "launches": r19["kernel_launches"]["collide"],
                                 "gbs": achieved},
                     "psi": {"avg_ms": psi_ms, "launches": r19["kernel_launches"]["psi"],
