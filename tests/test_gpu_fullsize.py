@@ -1,5 +1,5 @@
 """Full-size checks in the launch configuration bench.py times: the 256^3 at-scale workload with
-automatic z-chunks (each collide block marches through ~29 planes).  Sampled cells are compared
+automatic z-chunks (each collide block marches through 32 planes on D3Q19, 26 on D3Q27).  Sampled cells are compared
 with the oracle, which advances a small periodic sub-box around each sample: after one step a
 cell depends only on the initial state within two cells (psi stencil of its pull sources), after
 two steps within four, so a sub-box of radius 3 / 5 closed by walls reproduces the full-domain
@@ -86,3 +86,21 @@ def test_fullsize_conservation(workload, Q):
     sim.close()
     assert abs(s1[0] - s0[0]) < 1e-5 * s0[0]
     assert np.abs(s1[1:] - s0[1:]).max() < 1e-5 * s0[0]
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_fullsize_onepass_equals_two_pass(workload, Q):
+    # the one-pass step in its bench configuration reproduces the two-pass step bit for bit over
+    # both AA parities (compared on the device)
+    import torch
+    rho, u, wparams = workload
+    d = dict(lattice=Q, shape=SHAPE, **wparams)
+    a = U.run_gpu(d, rho, u, steps=3)
+    fa = a.populations()
+    a.close()
+    b = U.run_gpu(dict(d, onepass=True), rho, u, steps=3)
+    fb = b.populations()
+    b.close()
+    assert torch.equal(fa, fb)
+    del fa, fb
+    torch.cuda.empty_cache()
