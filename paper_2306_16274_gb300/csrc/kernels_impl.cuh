@@ -130,6 +130,28 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
     }
 }
 
+// the same plane in two halves: the loads into registers, then (an iteration later) the stores
+// into the ring slot, so that the loads' latency is spent on a plane's collision
+__device__ __forceinline__ void fetch_psi_plane(float (&v)[ZM_SLOTS], const float* __restrict__ psi, int zz, int nz,
+                                                int wall_z, uint32_t nxy, const uint32_t (&goff)[ZM_SLOTS],
+                                                const bool (&gok)[ZM_SLOTS], int tid) {
+    bool zok = true;
+    if (zz < 0) { zok = !wall_z; zz += nz; } else if (zz >= nz) { zok = !wall_z; zz -= nz; }
+    const uint32_t zb = (uint32_t)zz * nxy;
+#pragma unroll
+    for (int s = 0; s < ZM_SLOTS; ++s) {
+        const int k = tid + s * ZM_NT;
+        v[s] = (k < ZM_RP && zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
+    }
+}
+__device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_SLOTS], int tid) {
+#pragma unroll
+    for (int s = 0; s < ZM_SLOTS; ++s) {
+        const int k = tid + s * ZM_NT;
+        if (k < ZM_RP) slot[k] = v[s];
+    }
+}
+
 #ifndef LBM_ZM_PREFETCH
 #define LBM_ZM_PREFETCH 1
 #endif
@@ -138,7 +160,10 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 // locates population planes.  F16 (shifted FP16 store): the densities the slots were written
 // with (rsrc) follow the march in a second shared ring `rring`; outputs are written relative
 // to the cell's current density rown.
-template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, class GM, class A>
+// PSI_PF: the psi (and FP16 density) ring planes are loaded into registers one plane ahead and
+// stored into the ring at the next plane (the whole-grid kernels; the multi-domain kernels, which
+// have fewer registers to spare, load each plane just before its barrier).
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
                                              int z0, int zchunk, float (*ring)[ZM_RP], float (*rring)[ZM_RP],
@@ -191,9 +216,23 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
     }
 #endif
     const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
+    float pv[ZM_SLOTS], rv[ZM_SLOTS];
+    if (PSI_PF && MULTIPHASE) fetch_psi_plane(pv, psi, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+    if (PSI_PF && F16) fetch_psi_plane(rv, rsrc, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
     for (int z = z0, j = 0; z < zend; ++z, ++j) {
-        if (MULTIPHASE) load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
-        if (F16) load_psi_plane(rring[(j + 2) & 3], rsrc, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        if (PSI_PF) {
+            if (MULTIPHASE) {
+                put_psi_plane(ring[(j + 2) & 3], pv, tid);
+                if (z + 1 < zend) fetch_psi_plane(pv, psi, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
+            }
+            if (F16) {
+                put_psi_plane(rring[(j + 2) & 3], rv, tid);
+                if (z + 1 < zend) fetch_psi_plane(rv, rsrc, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
+            }
+        } else {
+            if (MULTIPHASE) load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+            if (F16) load_psi_plane(rring[(j + 2) & 3], rsrc, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        }
         if (MULTIPHASE || F16) __syncthreads();
         if (!act_xy) continue;
 #if LBM_ZM_PREFETCH
@@ -243,7 +282,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     __shared__ float ring[F16 ? 8 : 4][ZM_RP];
     const KGeom g{kp};
     const PlanePtrsT<typename std::conditional<F16, __half, float>::type> addr{kp};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE, F16>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
+    collide_tile<PARITY, SOLIDS, MULTIPHASE, F16, true>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
                                                   blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring, ring + 4,
                                                   rsrc, rown);
 }
@@ -375,7 +414,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
+    collide_tile<PARITY, SOLIDS, MULTIPHASE, false, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
                                                     ring, nullptr, nullptr, nullptr);
 }
 
