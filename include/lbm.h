@@ -120,10 +120,12 @@ typedef struct {
                             /* join a batch.                                                 */
     int32_t onepass;        /* 1: one pass per step over two population copies (read one,    */
                             /* write the other, pull streaming): the collide pass computes   */
-                            /* rho and psi of each tile and a one-cell halo itself, so no    */
-                            /* separate density/psi pass and no psi field are needed; same   */
-                            /* results bit for bit, twice the population memory.  Periodic  */
-                            /* boundaries, no solid mask, FP32 store; cannot join a batch.   */
+                            /* rho and psi of each tile and a one-cell border itself, so a   */
+                            /* step has no separate density/psi pass (psi is formed on       */
+                            /* demand for lbm_get_psi / lbm_get_moments); same results bit   */
+                            /* for bit, twice the population memory.  Periodic boundaries,   */
+                            /* no solid mask, FP32 store; cannot join a batch.  0: the       */
+                            /* in-place two-pass step (default).                             */
 } lbm_params;
 
 /* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,
@@ -199,8 +201,9 @@ size_t lbm_device_bytes(const lbm_ctx* ctx);
 
 /* Device bytes a context created from *params holds after lbm_init_fields
  * with device pointers (with_solid != 0: with a solid mask), without creating
- * it: the populations (Q planes padded to 64 cells), psi, the status word and
- * the reduction scratch, plus 5 bytes per cell for a mask.  For admission
+ * it: the populations (Q planes padded to 64 cells; two copies with onepass,
+ * half-size slots with the FP16 store plus two FP32 density fields), psi, the
+ * status word and the reduction scratch, plus 5 bytes per cell for a mask.  For admission
  * control under a memory budget; the paper has no counterpart.  Errors: as
  * lbm_create's validation (LBM_ERR_ARG), bytes == NULL. */
 lbm_status lbm_estimate_bytes(const lbm_params* params, int32_t with_solid, size_t* bytes);
