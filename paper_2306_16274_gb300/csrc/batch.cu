@@ -66,6 +66,7 @@ KParams physics_of(const KParams& k) {
     for (float*& q : p.fq) q = nullptr;
     for (float*& q : p.gq) q = nullptr;
     p.zchunk = 0;
+    p.zlo = p.zhi = 0;
     return p;
 }
 

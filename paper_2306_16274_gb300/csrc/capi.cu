@@ -152,6 +152,8 @@ KParams derive(const lbm_params& p, long long plane) {
     k.gy = (float)p.g[1];
     k.gz = (float)p.g[2];
     k.zchunk = p.zchunk;
+    k.zlo = 0;
+    k.zhi = p.nz;
     return k;
 }
 
@@ -191,10 +193,34 @@ cudaError_t run_onepass(lbm_ctx* c) {
     return e;
 }
 
+// Walls only at the two z ends (the droplet-impact setup): the planes between them need no
+// solid handling, so they take the solid-free kernel and only the two wall planes the solid one.
+bool zwalls_only(const lbm_ctx* c) {
+    return !c->nbmask && !c->kp.wall_x && !c->kp.wall_y && c->kp.wall_z && c->kp.nz >= 3 && !c->onepass;
+}
+
+cudaError_t launch_collide(const lbm_ctx* c, const lbm::KParams& k, int solids) {
+    return c->Q == 19 ? lbm::launch_collide_q19(k, c->parity, solids, bufs(c), c->stream)
+                      : lbm::launch_collide_q27(k, c->parity, solids, bufs(c), c->stream);
+}
+
 cudaError_t run_collide(lbm_ctx* c) {
-    const int s = has_solids(c);
-    cudaError_t e = c->Q == 19 ? lbm::launch_collide_q19(c->kp, c->parity, s, bufs(c), c->stream)
-                               : lbm::launch_collide_q27(c->kp, c->parity, s, bufs(c), c->stream);
+    cudaError_t e;
+    if (zwalls_only(c)) {
+        // each slot is read and written by one cell only, so the three plane ranges are independent
+        lbm::KParams k = c->kp;
+        k.zlo = 1;
+        k.zhi = k.nz - 1;
+        e = launch_collide(c, k, 0);
+        k.zlo = 0;
+        k.zhi = 1;
+        if (e == cudaSuccess) e = launch_collide(c, k, 1);
+        k.zlo = k.nz - 1;
+        k.zhi = k.nz;
+        if (e == cudaSuccess) e = launch_collide(c, k, 1);
+    } else {
+        e = launch_collide(c, c->kp, has_solids(c));
+    }
     if (c->f16) c->rs ^= 1;   // the slots are now relative to the densities the collide pass used
     return e;
 }
@@ -430,7 +456,7 @@ lbm_status lbm_step(lbm_ctx* c, int32_t n) {
         }
         return LBM_OK;
     }
-    if (has_solids(c) && !c->timing && !c->f16 && n > 0 &&
+    if (has_solids(c) && !zwalls_only(c) && !c->timing && !c->f16 && n > 0 &&
         (unsigned long long)c->Q * (unsigned long long)c->kp.plane <= 0xFFFFFFFFull) {
         // walls or solids: the tile path, which runs solid-free tiles without solid handling
         if (!c->self_batch) {

@@ -166,14 +166,14 @@ __device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_S
 template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
-                                             int z0, int zchunk, float (*ring)[ZM_RP], float (*rring)[ZM_RP],
+                                             int z0, int zchunk, int zmax, float (*ring)[ZM_RP], float (*rring)[ZM_RP],
                                              const float* __restrict__ rsrc, const float* __restrict__ rown) {
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
     const int x = x0 + tx, y = y0 + ty;
     const int nx = g.nx(), ny = g.ny(), nz = g.nz();
     const bool act_xy = x < nx && y < ny;
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
-    const int zend = min(z0 + zchunk, nz);
+    const int zend = min(z0 + zchunk, zmax);
 
     uint32_t goff[ZM_SLOTS];
     bool gok[ZM_SLOTS];
@@ -283,8 +283,8 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams k
     const KGeom g{kp};
     const PlanePtrsT<typename std::conditional<F16, __half, float>::type> addr{kp};
     collide_tile<PARITY, SOLIDS, MULTIPHASE, F16, true>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
-                                                  blockIdx.y * ZM_BY, blockIdx.z * zchunk, zchunk, ring, ring + 4,
-                                                  rsrc, rown);
+                                                        blockIdx.y * ZM_BY, kp.zlo + (int)blockIdx.z * zchunk,
+                                                        zchunk, kp.zhi, ring, ring + 4, rsrc, rown);
 }
 
 // ---- one-pass update with two population copies (periodic domains without solids, FP32).
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const DGeom g{m};
     const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
     collide_tile<PARITY, SOLIDS, MULTIPHASE, false, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
-                                                    ring, nullptr, nullptr, nullptr);
+                                                           g.nz(), ring, nullptr, nullptr, nullptr);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -778,8 +778,9 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
 // costs about h planes' worth of extra time at its start (the psi planes below and at its first
 // plane, the first loads with nothing to overlap them).  Over the chunk counts that give at
 // least three waves, the choice minimises (1 + h / zc) x ceil(waves) / waves.
-static int choose_zchunk(const KParams& kp, double h) {
-    if (kp.zchunk > 0) return kp.zchunk < kp.nz ? kp.zchunk : kp.nz;
+static int choose_zchunk(const KParams& kp, double h, int nz) {
+    if (kp.zchunk > 0) return kp.zchunk < nz ? kp.zchunk : nz;
+    if (nz <= 1) return 1;
     static const int sms = [] {
         int dev = 0, n = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
@@ -789,18 +790,18 @@ static int choose_zchunk(const KParams& kp, double h) {
     }();
     thread_local long long key[4] = {-1, -1, -1, -1};
     thread_local int cached = 1;
-    const long long k[4] = {kp.nx, kp.ny, kp.nz, (long long)(h * 1024.0)};
+    const long long k[4] = {kp.nx, kp.ny, nz, (long long)(h * 1024.0)};
     if (k[0] == key[0] && k[1] == key[1] && k[2] == key[2] && k[3] == key[3]) return cached;
     const double cap = (double)sms * ZM_MINB;
     const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + ZM_BY - 1) / ZM_BY);
-    int best = kp.nz;
+    int best = nz;
     double best_cost = 1e300;
-    for (int c = 1; c <= kp.nz; ++c) {
-        const int zc = (kp.nz + c - 1) / c;
-        const int chunks = (kp.nz + zc - 1) / zc;
+    for (int c = 1; c <= nz; ++c) {
+        const int zc = (nz + c - 1) / c;
+        const int chunks = (nz + zc - 1) / zc;
         if (chunks != c) continue;                 // the same split as a smaller count
         const double waves = (double)(cols * chunks) / cap;
-        if (waves < 3.0 && c < kp.nz) continue;
+        if (waves < 3.0 && c < nz) continue;
         const double cost = (1.0 + h / zc) * std::ceil(waves) / waves;
         if (cost < best_cost - 1e-9) { best_cost = cost; best = zc; }
     }
@@ -809,12 +810,14 @@ static int choose_zchunk(const KParams& kp, double h) {
     return best;
 }
 
-static int collide_zchunk(const KParams& kp) { return choose_zchunk(kp, 1.0); }
+// over the planes [zlo, zhi) the whole-grid collide kernels march through
+static int collide_zchunk(const KParams& kp) { return choose_zchunk(kp, 1.0, kp.zhi - kp.zlo); }
 
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B,
                                              cudaStream_t st) {
     const int zc = collide_zchunk(kp);
-    const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
+    const int planes = kp.zhi - kp.zlo;
+    const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (planes + zc - 1) / zc), b(ZM_BX, ZM_BY);
     const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
     return B.f16 ? launch_collide_store<true>(g, b, st, kp, B, zc, key)
                  : launch_collide_store<false>(g, b, st, kp, B, zc, key);
@@ -866,7 +869,7 @@ cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, cons
 
 cudaError_t LBM_CAT(launch_onepass_q, LBM_Q)(const KParams& kp, unsigned* status, cudaStream_t st) {
     // a chunk starts with two psi planes whose loads nothing overlaps
-    const int zc = choose_zchunk(kp, 1.5);
+    const int zc = choose_zchunk(kp, 1.5, kp.nz);
     const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
     if (kp.multiphase) collide_onepass_kernel<true, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);
     else collide_onepass_kernel<false, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);

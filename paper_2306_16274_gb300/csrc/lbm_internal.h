@@ -41,6 +41,7 @@ struct KParams {
     float gx, gy, gz;             // body force per unit mass
     float* fq[27];                // base of population plane i (f + i * plane); cells < 2^31
     int zchunk;                   // z planes per collide block (0 = automatic)
+    int zlo, zhi;                 // planes [zlo, zhi) the whole-grid collide kernels march through
     float* gq[27];                // one-pass layout: planes of the copy the step writes
 };
 

@@ -171,3 +171,23 @@ def test_single_domain_tile_path_equals_grid_path(which):
         assert np.array_equal(tiles.populations().cpu().numpy(), grid.populations().cpu().numpy())
     ms, launches = grid.kernel_timing()
     assert launches["collide"] == 47 and launches["psi"] == 47
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("shape,zchunk", [((40, 20, 3), 0), ((33, 17, 26), 0), ((33, 17, 26), 5)])
+def test_zwall_domain_split_equals_batch(Q, shape, zchunk):
+    # a domain with walls only at the z ends steps its inner planes with the solid-free kernel and
+    # the two wall planes with the solid kernel; stepping it alone must equal stepping it as the
+    # only member of a batch (tiles classified by solid need) bit for bit
+    from paper_2306_16274_gb300 import Batch
+    kw, rl, rv = U.cs_eos("T0.7")
+    nx, ny, nz = shape
+    rho, u = W.impact(shape, min(nx, ny, 2 * nz) / 5.0, rl, rv, U=0.05, gap=0.5)
+    d = dict(lattice=Q, shape=shape, bc=(0, 0, 1), sigma=0.1, kappa=0.3, G_ads=0.1, zchunk=zchunk, **kw)
+    a = U.run_gpu(d, rho, u, steps=0)
+    b = U.run_gpu(d, rho, u, steps=0)
+    bb = Batch([b])
+    for n in (1, 4, 9):
+        a.step(n)
+        bb.step(n)
+        assert np.array_equal(a.populations(device=False), b.populations(device=False)), (n,)
