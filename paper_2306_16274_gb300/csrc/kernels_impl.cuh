@@ -161,8 +161,8 @@ __device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_S
 // with (rsrc) follow the march in a second shared ring `rring`; outputs are written relative
 // to the cell's current density rown.
 // PSI_PF: the psi (and FP16 density) ring planes are loaded into registers one plane ahead and
-// stored into the ring at the next plane (the whole-grid kernels; the multi-domain kernels, which
-// have fewer registers to spare, load each plane just before its barrier).
+// stored into the ring at the next plane (all but the multi-domain kernels' solid tiles, which
+// have no registers to spare and load each plane just before its barrier).
 template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
@@ -413,8 +413,8 @@ __global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KPa
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
-    const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE, false, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
+    const DomPlanes addr{m};
+    collide_tile<PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
                                                            g.nz(), ring, nullptr, nullptr, nullptr);
 }
 

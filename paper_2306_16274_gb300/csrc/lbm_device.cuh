@@ -473,6 +473,15 @@ struct PlaneIdx32 {
         return const_cast<float*>(base) + (uint32_t)((uint32_t)i * plane + off);
     }
 };
+// ... or the member record itself: the plane stride is read from the (constant-bank) record at each
+// use instead of being held in a register, which leaves the multi-domain collide kernel registers
+// for the psi-ring prefetch.
+struct DomPlanes {
+    const BatchDom& d;
+    __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
+        return d.base + (uint32_t)((uint32_t)i * (uint32_t)d.plane + off);
+    }
+};
 
 struct RsOff32 {
     const float* r;
