@@ -778,7 +778,7 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
 // costs about h planes' worth of extra time at its start (the psi planes below and at its first
 // plane, the first loads with nothing to overlap them).  Over the chunk counts that give at
 // least three waves, the choice minimises (1 + h / zc) x ceil(waves) / waves.
-static int choose_zchunk(const KParams& kp, double h, int nz) {
+static int choose_zchunk(const KParams& kp, double h, int nz, int by = ZM_BY, int minb = ZM_MINB) {
     if (kp.zchunk > 0) return kp.zchunk < nz ? kp.zchunk : nz;
     if (nz <= 1) return 1;
     static const int sms = [] {
@@ -790,10 +790,10 @@ static int choose_zchunk(const KParams& kp, double h, int nz) {
     }();
     thread_local long long key[4] = {-1, -1, -1, -1};
     thread_local int cached = 1;
-    const long long k[4] = {kp.nx, kp.ny, nz, (long long)(h * 1024.0)};
+    const long long k[4] = {kp.nx, kp.ny, nz, (long long)(h * 1024.0) + 4096LL * (by + 64LL * minb)};
     if (k[0] == key[0] && k[1] == key[1] && k[2] == key[2] && k[3] == key[3]) return cached;
-    const double cap = (double)sms * ZM_MINB;
-    const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + ZM_BY - 1) / ZM_BY);
+    const double cap = (double)sms * minb;
+    const long long cols = (long long)((kp.nx + ZM_BX - 1) / ZM_BX) * ((kp.ny + by - 1) / by);
     int best = nz;
     double best_cost = 1e300;
     for (int c = 1; c <= nz; ++c) {
@@ -867,12 +867,16 @@ cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, cons
     return cudaGetLastError();
 }
 
+// one-pass tiles: 32 x 4 cells (the 76-cell border fits the 128 threads), 7 (D3Q19) / 5 (D3Q27)
+// blocks per SM -- the best of 32 x 4 / 8 / 16 tiles and 4-8 blocks per SM, measured
+constexpr int OP_BY = 4, OP_MINB = LBM_Q == 19 ? 7 : 5;
+
 cudaError_t LBM_CAT(launch_onepass_q, LBM_Q)(const KParams& kp, unsigned* status, cudaStream_t st) {
     // a chunk starts with two psi planes whose loads nothing overlaps
-    const int zc = choose_zchunk(kp, 1.5, kp.nz);
-    const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (kp.nz + zc - 1) / zc), b(ZM_BX, ZM_BY);
-    if (kp.multiphase) collide_onepass_kernel<true, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);
-    else collide_onepass_kernel<false, ZM_BY, ZM_MINB><<<g, b, 0, st>>>(kp, status, zc);
+    const int zc = choose_zchunk(kp, 1.5, kp.nz, OP_BY, OP_MINB);
+    const dim3 g((kp.nx + 31) / 32, (kp.ny + OP_BY - 1) / OP_BY, (kp.nz + zc - 1) / zc), b(32, OP_BY);
+    if (kp.multiphase) collide_onepass_kernel<true, OP_BY, OP_MINB><<<g, b, 0, st>>>(kp, status, zc);
+    else collide_onepass_kernel<false, OP_BY, OP_MINB><<<g, b, 0, st>>>(kp, status, zc);
     return cudaGetLastError();
 }
 
