@@ -17,7 +17,7 @@ follows the paper's order:
 7. f_bar_i(x + e_i, t + 1) = f_bar*_i(x, t)               (Eq. e9), half-way
    bounce-back where x + e_i is solid: f_bar_ibar(x, t+1) = f_bar*_i(x, t).
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 * s_e in Eq. e17 is the rate of m_7 (s2b); s_nu is the shear rate s2 (per cell when
   the viscosity varies with density, Sec. IV A).
 * F_int in the sigma term of Eq. e17 is the interaction force alone.
