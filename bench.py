@@ -631,9 +631,12 @@ def main():
     if r27:
         ab27 = algorithmic_bytes(27)
         c27 = r27["kernel_ms"]["collide"] / max(r27["kernel_launches"]["collide"], 1)
+        p27 = r27["kernel_ms"]["psi"] / max(r27["kernel_launches"]["psi"], 1)
         line["d3q27"] = {"value": r27["mlups_local"], "unit": UNIT, "ms_per_step": r27["ms"] / args.steps,
                          "hbm_frac_step": ab27["step"] * n * args.steps / (r27["ms"] * 1e-3) / 1e9 / peak,
-                         "collide_gbs": ab27["collide"] * n / (c27 * 1e-3) / 1e9, "mass_drift_rel": r27["mass_drift"]}
+                         "collide_gbs": ab27["collide"] * n / (c27 * 1e-3) / 1e9, "collide_avg_ms": c27,
+                         "psi_gbs": ab27["psi"] * n / (p27 * 1e-3) / 1e9 if p27 > 0 else None,
+                         "psi_avg_ms": p27, "mass_drift_rel": r27["mass_drift"]}
     if e2e:
         line["e2e"] = e2e
     if f16:
