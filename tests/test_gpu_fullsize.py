@@ -104,3 +104,52 @@ def test_fullsize_onepass_equals_two_pass(workload, Q):
     assert torch.equal(fa, fb)
     del fa, fb
     torch.cuda.empty_cache()
+
+
+def test_largest_domain_near_the_cell_limit():
+    # 1290^3 = 2,146,689,000 cells, just under the 2^31 - 1 cells that 32-bit cell offsets allow
+    # (D3Q19 populations 163 GB): two steps of a C-S field, sampled cells (among them the last
+    # cell and the far corners) against the oracle on wall-closed sub-boxes, and mass conservation
+    import torch
+    n = 1290
+    free, _ = torch.cuda.mem_get_info()
+    if free < 215e9:
+        pytest.skip(f"needs ~210 GB of free device memory, {free / 1e9:.0f} GB free")
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=19, shape=(n, n, n), sigma=0.1, kappa=0.3, **kw)
+    gen = torch.Generator(device="cuda").manual_seed(2306)
+    rho = 0.2 + 0.02 * torch.rand((n, n, n), device="cuda", generator=gen)
+    u = 0.01 * (torch.rand((3, n, n, n), device="cuda", generator=gen) - 0.5)
+    samples = np.array([[n - 1, n - 1, n - 1], [0, 0, 0], [n - 1, 0, n - 1], [0, n - 1, 0],
+                        [n // 2, 7, n - 3], [1111, 1289, 3]])
+    radius, steps = 5, 2
+    windows = []
+    for c in samples:
+        idx = [torch.tensor([(int(v) + k) % n for k in range(-radius, radius + 1)], device="cuda") for v in c]
+        r = rho.index_select(0, idx[0]).index_select(1, idx[1]).index_select(2, idx[2])
+        uu = u.index_select(1, idx[0]).index_select(2, idx[1]).index_select(3, idx[2])
+        windows.append((r.double().cpu().numpy(), uu.double().cpu().numpy()))
+    from paper_2306_16274_gb300 import Simulation
+    sim = Simulation(U.gpu_params(d))
+    sim.init_fields(rho, u)
+    del rho, u
+    torch.cuda.empty_cache()
+    _, _, s0 = sim.moments(device=True)
+    torch.cuda.empty_cache()
+    sim.step(steps)
+    r_g, u_g, s1 = sim.moments(device=True)
+    t = torch.tensor(samples, device="cuda", dtype=torch.long)
+    rg = r_g[t[:, 0], t[:, 1], t[:, 2]].double().cpu().numpy()
+    ug = u_g[:, t[:, 0], t[:, 1], t[:, 2]].double().cpu().numpy()
+    del r_g, u_g
+    sim.close()
+    torch.cuda.empty_cache()
+    m = 2 * radius + 1
+    for k, (r, uu) in enumerate(windows):
+        dd = dict(d)
+        dd["shape"] = (m, m, m)
+        dd["bc"] = (1, 1, 1)
+        ro, uo = U.run_oracle(dd, r, uu, steps=steps).moments()
+        assert abs(rg[k] - ro[radius, radius, radius]) < 2e-6 * ro[radius, radius, radius], (tuple(samples[k]),)
+        assert np.abs(ug[:, k] - uo[:, radius, radius, radius]).max() < 2e-6, (tuple(samples[k]),)
+    assert abs(s1[0] - s0[0]) < 1e-6 * s0[0]
