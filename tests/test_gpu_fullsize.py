@@ -153,3 +153,34 @@ def test_largest_domain_near_the_cell_limit():
         assert abs(rg[k] - ro[radius, radius, radius]) < 2e-6 * ro[radius, radius, radius], (tuple(samples[k]),)
         assert np.abs(ug[:, k] - uo[:, radius, radius, radius]).max() < 2e-6, (tuple(samples[k]),)
     assert abs(s1[0] - s0[0]) < 1e-6 * s0[0]
+
+
+@pytest.mark.parametrize("shape", [(65535, 3, 2), (2, 5, 65535)])
+def test_maximum_extent(shape):
+    # an axis at LBM_MAX_EXTENT (the psi pass launches one block row per z plane): two steps of a
+    # C-S field, cells at both ends of the long axis against the oracle on wall-closed sub-boxes
+    import torch
+    nx, ny, nz = shape
+    kw, rl, rv = U.cs_eos("T0.7")
+    d = dict(lattice=27, shape=shape, sigma=0.1, **kw)
+    rng = np.random.default_rng(65535)
+    rho = 0.2 + 0.02 * rng.random((nz, ny, nx))
+    u = 0.01 * (rng.random((3, nz, ny, nx)) - 0.5)
+    radius, steps = 5, 2
+    sim = U.run_gpu(d, rho, u, steps=steps)
+    r_g, u_g, _ = sim.moments(device=False)
+    sim.close()
+    long_axis = int(np.argmax(shape))
+    n_long = shape[long_axis]
+    for pos in (0, 1, n_long // 2, n_long - 2, n_long - 1):
+        c = [0, 0, 0]                     # (x, y, z)
+        c[long_axis] = pos
+        x, y, z = c
+        idx = [np.arange(v - radius, v + radius + 1) % size for v, size in ((z, nz), (y, ny), (x, nx))]
+        r = rho[np.ix_(*idx)]
+        uu = u[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]]
+        m = 2 * radius + 1
+        dd = dict(d, shape=(m, m, m), bc=(1, 1, 1))
+        ro, uo = U.run_oracle(dd, r, uu, steps=steps).moments()
+        assert abs(r_g[z, y, x] - ro[radius, radius, radius]) < 2e-6 * ro[radius, radius, radius], (c,)
+        assert np.abs(u_g[:, z, y, x] - uo[:, radius, radius, radius]).max() < 2e-6, (c,)
