@@ -126,3 +126,18 @@ def test_onepass_status_words():
     with pytest.raises(LBMError) as e:
         sim.sync()
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 16), (1, 5, 1), (2, 3, 1), (33, 1, 2)])
+def test_onepass_degenerate_extents(Q, shape):
+    # extents of 1 and 2 cells: a tile's border wraps onto the tile itself
+    kw, rl, rv = U.cs_eos("T0.7")
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    rho = 0.2 + 0.02 * rng.random((nz, ny, nx))
+    u = 0.01 * (rng.random((3, nz, ny, nx)) - 0.5)
+    d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.3, **kw)
+    a = U.run_gpu(d, rho, u, steps=5)
+    b = U.run_gpu(dict(d, onepass=True), rho, u, steps=5)
+    assert np.array_equal(a.populations(device=False), b.populations(device=False))
