@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step)"
+METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step); batched p50/p99 job latency"
 UNIT = "MLUPS"
 SHAPE = (256, 256, 256)
 WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves the EOS range within 100 steps "
