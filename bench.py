@@ -669,6 +669,13 @@ def main():
         line["batched"] = batched
     if serving:
         line["serving"] = serving
+        po = serving.get("poisson", {})
+        if "batched" in po and "one_at_a_time" in po:
+            # the metric's second part: time-to-result of the request stream under Poisson arrivals
+            line["job_latency"] = {
+                "unit": "s", "arrivals": "Poisson at 0.8 of the one-at-a-time service rate",
+                "batched": {"p50": po["batched"]["p50_s"], "p99": po["batched"]["p99_s"]},
+                "one_at_a_time": {"p50": po["one_at_a_time"]["p50_s"], "p99": po["one_at_a_time"]["p99_s"]}}
     if ws == 1 and not args.no_cpu_baseline:
         try:
             cores = host_cores()
