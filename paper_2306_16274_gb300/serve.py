@@ -193,7 +193,8 @@ class GpuEngine:
     """Runs jobs through liblbm.so on the current CUDA device, all on one stream.
 
     batched=True advances the resident jobs with one multi-domain Batch (rebuilt when the set
-    changes); batched=False steps each job with its own single-domain launches.  keep_populations:
+    changes; a lone job steps alone); batched=False steps each job with its own single-domain
+    launches.  keep_populations:
     copy every finished job's populations to the host (for equality checks)."""
 
     def __init__(self, batched=True, stream=None, keep_populations=False):
@@ -235,7 +236,12 @@ class GpuEngine:
         sim.close()
 
     def advance(self, sims, n):
-        if not self.batched:
+        if not self.batched or len(sims) == 1:
+            # a lone resident job takes its own single-domain launches (the whole-grid kernels
+            # where its geometry allows), faster than a one-member batch; results are the same
+            if self._batch is not None:
+                self._batch.close()
+                self._batch, self._batch_key = None, None
             for s in sims:
                 s.step(n)
             self.launch_sets += len(sims)
