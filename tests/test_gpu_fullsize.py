@@ -1,5 +1,5 @@
 """Full-size checks in the launch configuration bench.py times: the 256^3 at-scale workload with
-automatic z-chunks (each collide block marches through 32 planes on D3Q19, 26 on D3Q27).  Sampled cells are compared
+automatic z-chunks (each collide block marches through 26 planes on D3Q19, 20 on D3Q27).  Sampled cells are compared
 with the oracle, which advances a small periodic sub-box around each sample: after one step a
 cell depends only on the initial state within two cells (psi stencil of its pull sources), after
 two steps within four, so a sub-box of radius 3 / 5 closed by walls reproduces the full-domain
