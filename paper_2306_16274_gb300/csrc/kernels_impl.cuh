@@ -197,16 +197,10 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
     o.yo[1] = (uint32_t)y * (uint32_t)nx;
     o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
 
-    if (MULTIPHASE) {
-        load_psi_plane(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
-        load_psi_plane(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
-    }
-    if (F16) {
-        load_psi_plane(rring[0], rsrc, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
-        load_psi_plane(rring[1], rsrc, z0, nz, g.wall_z(), nxy, goff, gok, tid);
-    }
 #if LBM_ZM_PREFETCH
-    // populations of the first plane, then of plane z+1 while plane z is computed
+    // populations of the first plane, then of plane z+1 while plane z is computed; the first
+    // plane's loads are issued before the ring's first planes are loaded and stored, so that the
+    // chunk's start-up waits for one round trip instead of two
     float pn[Q];
     uint32_t bits_n = 0u;
     if (act_xy) {
@@ -215,10 +209,18 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(addr, o, bits_n, pn);
     }
 #endif
-    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
     float pv[ZM_SLOTS], rv[ZM_SLOTS];
     if (PSI_PF && MULTIPHASE) fetch_psi_plane(pv, psi, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
     if (PSI_PF && F16) fetch_psi_plane(rv, rsrc, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+    if (MULTIPHASE) {
+        load_psi_plane(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
+    }
+    if (F16) {
+        load_psi_plane(rring[0], rsrc, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane(rring[1], rsrc, z0, nz, g.wall_z(), nxy, goff, gok, tid);
+    }
+    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
     for (int z = z0, j = 0; z < zend; ++z, ++j) {
         if (PSI_PF) {
             if (MULTIPHASE) {
