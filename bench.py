@@ -674,8 +674,10 @@ def main():
             # the metric's second part: time-to-result of the request stream under Poisson arrivals
             line["job_latency"] = {
                 "unit": "s", "arrivals": "Poisson at 0.8 of the one-at-a-time service rate",
-                "batched": {"p50": po["batched"]["p50_s"], "p99": po["batched"]["p99_s"]},
-                "one_at_a_time": {"p50": po["one_at_a_time"]["p50_s"], "p99": po["one_at_a_time"]["p99_s"]}}
+                "batched": {"p50": po["batched"]["p50_s"], "p99": po["batched"]["p99_s"],
+                            "mean": po["batched"]["mean_s"]},
+                "one_at_a_time": {"p50": po["one_at_a_time"]["p50_s"], "p99": po["one_at_a_time"]["p99_s"],
+                                  "mean": po["one_at_a_time"]["mean_s"]}}
     if ws == 1 and not args.no_cpu_baseline:
         try:
             cores = host_cores()
