@@ -184,3 +184,23 @@ def test_maximum_extent(shape):
         ro, uo = U.run_oracle(dd, r, uu, steps=steps).moments()
         assert abs(r_g[z, y, x] - ro[radius, radius, radius]) < 2e-6 * ro[radius, radius, radius], (c,)
         assert np.abs(u_g[:, z, y, x] - uo[:, radius, radius, radius]).max() < 2e-6, (c,)
+
+
+def test_allocation_failure_is_reported():
+    # a context larger than the device (two D3Q27 population copies of 1290^3 cells, ~470 GB):
+    # lbm_create frees what it allocated and returns LBM_ERR_OOM; the device stays usable
+    import torch
+    from paper_2306_16274_gb300 import LBMError, Simulation
+    _, total = torch.cuda.mem_get_info()
+    p = U.gpu_params(dict(lattice=27, shape=(1290, 1290, 1290), onepass=True))
+    from paper_2306_16274_gb300 import estimate_bytes
+    if estimate_bytes(p) <= total:
+        pytest.skip("the device is large enough for this context")
+    free0, _ = torch.cuda.mem_get_info()
+    with pytest.raises(LBMError) as e:
+        Simulation(p)
+    assert e.value.status == 2
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20)
+    sim = U.run_gpu(dict(lattice=19, shape=(8, 8, 8)), np.ones((8, 8, 8)), np.zeros((3, 8, 8, 8)), steps=2)
+    sim.sync()
