@@ -301,6 +301,13 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 /* Name of a status code. */
 const char* lbm_status_string(lbm_status s);
 
+/* Debugging aid (the paper has no counterpart): a library compiled with LBM_BOUNDS_CHECK=1 checks
+ * every population, psi and psi-ring access of the step kernels against its array before making
+ * it; an access outside is counted and redirected to the array's first element instead of being
+ * made.  Returns the count since the library was loaded, on the current device; 0 in the normal
+ * build, where the checks are compiled away. */
+uint64_t lbm_debug_bounds_violations(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,31 @@ def build(force=False, verbose=False, ptxas_verbose=False):
     return LIB
 
 
+def build_variant(outdir, defines):
+    """Compile the library with extra preprocessor definitions (e.g. -DLBM_BOUNDS_CHECK=1) into
+    outdir/liblbm.so, always from scratch; returns the path.  For debugging builds, next to the
+    normal in-tree one."""
+    os.makedirs(outdir, exist_ok=True)
+    cc = nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(outdir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *defines, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    lib = os.path.join(outdir, "liblbm.so")
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", lib] + objs
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return lib
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")

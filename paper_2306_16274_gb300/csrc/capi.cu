@@ -654,6 +654,10 @@ const char* lbm_last_error(const lbm_ctx* c) {
     return c->err.c_str();
 }
 
+uint64_t lbm_debug_bounds_violations(void) {
+    return lbm::bounds_violations_q19() + lbm::bounds_violations_q27();
+}
+
 const char* lbm_status_string(lbm_status s) {
     switch (s) {
         case LBM_OK: return "LBM_OK";

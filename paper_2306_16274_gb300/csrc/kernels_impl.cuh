@@ -42,7 +42,7 @@ __device__ __forceinline__ void psi_column(const KParams& kp, const GM& g, const
         o.c = o.zo[1] + o.yo[1] + o.xo[1];
         const uint32_t bits = SOLIDS ? solid_bits32<Q>(g, nbmask, o.c, x, y, z) : 0u;
         if (bits & 1u) {
-            if (kp.multiphase) psi[o.c] = 0.0f;
+            if (kp.multiphase) psi[bounded(o.c, (unsigned long long)nxy * nz)] = 0.0f;
             if (F16) rdst[o.c] = 1.0f;
             continue;
         }
@@ -53,7 +53,7 @@ __device__ __forceinline__ void psi_column(const KParams& kp, const GM& g, const
 #pragma unroll
         for (int i = 0; i < Q; ++i) rho += p[i];
         if (F16) rdst[o.c] = rho;
-        if (kp.multiphase) psi[o.c] = eval_psi(kp, rho, status);
+        if (kp.multiphase) psi[bounded(o.c, (unsigned long long)nxy * nz)] = eval_psi(kp, rho, status);
     }
 }
 
@@ -126,7 +126,7 @@ __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restr
 #pragma unroll
     for (int s = 0; s < ZM_SLOTS; ++s) {
         const int k = tid + s * ZM_NT;
-        if (k < ZM_RP) slot[k] = (zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
+        if (k < ZM_RP) slot[k] = (zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
     }
 }
 
@@ -141,7 +141,7 @@ __device__ __forceinline__ void fetch_psi_plane(float (&v)[ZM_SLOTS], const floa
 #pragma unroll
     for (int s = 0; s < ZM_SLOTS; ++s) {
         const int k = tid + s * ZM_NT;
-        v[s] = (k < ZM_RP && zok && gok[s]) ? __ldg(psi + zb + goff[s]) : 0.0f;
+        v[s] = (k < ZM_RP && zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
     }
 }
 __device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_SLOTS], int tid) {
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) collide_onepass_kernel(const KP
         collide<Q>(kp, p, Fo, rho, ux, uy, uz);
         if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) kp.gq[i][o.c] = p[i];
+        for (int i = 0; i < Q; ++i) kp.gq[i][bounded(o.c, (unsigned long long)kp.ncell)] = p[i];
     }
 }
 
@@ -881,6 +881,16 @@ cudaError_t LBM_CAT(launch_onepass_q, LBM_Q)(const KParams& kp, unsigned* status
     if (kp.multiphase) collide_onepass_kernel<true, OP_BY, OP_MINB><<<g, b, 0, st>>>(kp, status, zc);
     else collide_onepass_kernel<false, OP_BY, OP_MINB><<<g, b, 0, st>>>(kp, status, zc);
     return cudaGetLastError();
+}
+
+unsigned long long LBM_CAT(bounds_violations_q, LBM_Q)() {
+#if LBM_BOUNDS_CHECK
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, lbm_bounds_count, sizeof(v)) != cudaSuccess) return ~0ull;
+    return v;
+#else
+    return 0;
+#endif
 }
 
 cudaError_t LBM_CAT(launch_pull_store_q, LBM_Q)(const KParams& kp, const float* fin, long long fstride, float* fout,

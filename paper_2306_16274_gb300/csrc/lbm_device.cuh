@@ -33,6 +33,28 @@
 
 namespace lbm {
 
+// ------------------------------------------------------------------ bounds-checked builds
+// Compiled with LBM_BOUNDS_CHECK=1, every population, psi and ring access of the step kernels is
+// checked against its array before it is made; an access outside is counted and redirected to
+// element 0 (no trap), and the count is read by lbm_debug_bounds_violations.  Other builds
+// compile the checks away.
+#ifndef LBM_BOUNDS_CHECK
+#define LBM_BOUNDS_CHECK 0
+#endif
+#if LBM_BOUNDS_CHECK
+static __device__ unsigned long long lbm_bounds_count;
+#endif
+__device__ __forceinline__ uint32_t bounded(uint32_t off, unsigned long long limit) {
+#if LBM_BOUNDS_CHECK
+    if ((unsigned long long)off >= limit) {
+        atomicAdd(&lbm_bounds_count, 1ull);
+        return 0u;
+    }
+#endif
+    (void)limit;
+    return off;
+}
+
 // ------------------------------------------------------------------ lattice (Eq. e1)
 __host__ __device__ constexpr int EX(int i) {
     constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
@@ -460,7 +482,15 @@ __device__ __forceinline__ uint32_t solid_bits32(const GM& g, const uint32_t* __
 template <class T>
 struct PlanePtrsT {
     const KParams& kp;
-    __device__ __forceinline__ T* ptr(int i, uint32_t off) const { return reinterpret_cast<T*>(kp.fq[i]) + off; }
+    __device__ __forceinline__ T* ptr(int i, uint32_t off) const {
+#if LBM_BOUNDS_CHECK
+        if (i < 0 || i >= 27 || !kp.fq[i]) {
+            atomicAdd(&lbm_bounds_count, 1ull);
+            i = 0;
+        }
+#endif
+        return reinterpret_cast<T*>(kp.fq[i]) + bounded(off, (unsigned long long)kp.ncell);
+    }
 };
 using PlanePtrs = PlanePtrsT<float>;
 // ... or, for multi-domain launches, one base pointer and a 32-bit plane stride: the whole
@@ -470,7 +500,7 @@ struct PlaneIdx32 {
     const float* base;
     uint32_t plane;
     __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
-        return const_cast<float*>(base) + (uint32_t)((uint32_t)i * plane + off);
+        return const_cast<float*>(base) + (uint32_t)((uint32_t)i * plane + bounded(off, plane));
     }
 };
 // ... or the member record itself: the plane stride is read from the (constant-bank) record at each
@@ -479,7 +509,8 @@ struct PlaneIdx32 {
 struct DomPlanes {
     const BatchDom& d;
     __device__ __forceinline__ float* ptr(int i, uint32_t off) const {
-        return d.base + (uint32_t)((uint32_t)i * (uint32_t)d.plane + off);
+        return d.base + (uint32_t)((uint32_t)i * (uint32_t)d.plane +
+                                   bounded(off, (unsigned long long)d.nx * d.ny * d.nz));
     }
 };
 

@@ -110,7 +110,8 @@ struct Bufs {
     cudaError_t launch_pull_store_q##Q(const KParams& kp, const float* fin, long long fstride,       \
                                        float* fout, cudaStream_t st);                               \
     int tile_height_q##Q();                                                                         \
-    int resident_blocks_q##Q();
+    int resident_blocks_q##Q();                                                                     \
+    unsigned long long bounds_violations_q##Q();
 
 LBM_DECLARE_LAUNCHERS(19)
 LBM_DECLARE_LAUNCHERS(27)

@@ -83,6 +83,7 @@ def lib():
         "lbm_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "lbm_batch_destroy": (V, [P]),
         "lbm_batch_last_error": (ctypes.c_char_p, [P]),
+        "lbm_debug_bounds_violations": (ctypes.c_uint64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
