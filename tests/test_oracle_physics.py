@@ -110,3 +110,58 @@ def test_laplace_law_and_surface_tension_scaling():
         assert d8 * 8 == pytest.approx(d12 * 12, rel=0.02)
         g[kappa] = 0.5 * (d8 * 8 + d12 * 12)
     assert g[0.5] / g[0.0] == pytest.approx(0.5, abs=0.05)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_variable_viscosity_sets_the_local_shear_rate(Q):
+    # Sec. IV A: nu(rho) = nu_v + (nu_l - nu_v)(rho - rho_v)/(rho_l - rho_v), each cell relaxing its
+    # shear moments at the s_nu that nu = (1/s_nu - 1/2) c_s^2 (text after Eq. e12) gives.  A shear wave
+    # in a uniform fluid of density rho0 then decays at nu(rho0) k^2.  Three densities: both ends of the
+    # interpolation (a swapped nu_l / nu_v fails) and one a quarter of the way (a non-linear or
+    # mis-anchored interpolation fails); the expected nu is written out from the stated numbers.
+    L = 64
+    rho_v, rho_l, nu_v, nu_l = 0.5, 1.5, 0.02, 0.2
+    k = 2 * np.pi / L
+    for rho0, nu in ((0.5, 0.02), (1.5, 0.2), (0.75, 0.065)):
+        p = lbm.Params(lattice=Q, shape=(1, 1, L), variable_nu=True, nu_l=nu_l, nu_v=nu_v,
+                       rho_l=rho_l, rho_v=rho_v)
+        s = lbm.State.from_fields(p, *W.shear_wave((1, 1, L), 1e-3, rho0=rho0))
+        a0 = np.abs(s.moments()[1][0]).max()
+        s.run(400)
+        a1 = np.abs(s.moments()[1][0]).max()
+        assert -np.log(a1 / a0) / 400 == pytest.approx(nu * k * k, rel=0.02), (rho0, nu)
+    # the rate itself, cell by cell, on a field spanning the range: 1 / (3 nu + 1/2)
+    p = lbm.Params(lattice=Q, variable_nu=True, nu_l=nu_l, nu_v=nu_v, rho_l=rho_l, rho_v=rho_v)
+    rho = np.array([0.5, 0.75, 1.0, 1.5])
+    assert np.allclose(lbm.shear_rate(rho, p), [1 / 0.56, 1 / 0.695, 1 / 0.83, 1 / 1.1], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
+def test_adsorption_force_magnitude_at_flat_walls(Q):
+    # Sec. III E: F_ads = -G_ads psi(x) sum_i w_i psi(x) s(x + e_i) e_i.  For a uniform fluid next to a
+    # flat wall the solid neighbours of a first-plane cell are the links with e_z = -1, whose weights
+    # add up to 1/2 on either lattice (D3Q19: 1/6 + 4/12; D3Q27: 2/9 + 4/18 + 4/72), so
+    # F_ads = (0, 0, +G_ads psi^2 / 2) at the bottom plane and -G_ads psi^2 / 2 at the top one.  On the
+    # edge where a y wall meets the z wall the solid links are those with e_y = -1 or e_z = -1: the z sum
+    # takes 1/2 from e_z = -1 and loses the links (e_y = -1, e_z = +1), 1/12 on either lattice (D3Q19:
+    # one edge link; D3Q27: 1/18 + 2/72), so F_z = 5/12 G_ads psi^2, and F_y likewise.  psi^2 is the
+    # square-root pseudopotential of Sec. II C, 2 (p_EOS - rho c_s^2) / G, with the C-S pressure.
+    t = W.constants()["cs"]["T0.7"]
+    c = W.constants()["cs"]
+    rho0, G, G_ads = 0.3, -1.0, 0.17
+    psi2 = 2.0 * (eos.cs_pressure(rho0, c["a"], c["b"], c["R"], t["T"]) - rho0 / 3.0) / G
+    assert 0.0 < psi2 < 0.5                  # psi^2 != psi: a wrong power of psi fails
+    shape = (4, 5, 6)
+    p = lbm.Params(lattice=Q, shape=shape, bc=(0, 0, 1), eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]),
+                   G=G, G_ads=G_ads)
+    s = lbm.State.from_fields(p, np.full((6, 5, 4), rho0), np.zeros((3, 6, 5, 4)))
+    F = s.fields()[2]["F_ads"]
+    assert np.allclose(F[2][0], 0.5 * G_ads * psi2, rtol=1e-13, atol=0)
+    assert np.allclose(F[2][-1], -0.5 * G_ads * psi2, rtol=1e-13, atol=0)
+    assert np.abs(F[:2]).max() < 1e-17 and np.abs(F[2][1:-1]).max() == 0.0
+    p.bc = (0, 1, 1)
+    s = lbm.State.from_fields(p, np.full((6, 5, 4), rho0), np.zeros((3, 6, 5, 4)))
+    F = s.fields()[2]["F_ads"]
+    assert np.allclose(F[1][0, 0], 5.0 / 12.0 * G_ads * psi2, rtol=1e-13, atol=0)   # bottom-front edge
+    assert np.allclose(F[2][0, 0], 5.0 / 12.0 * G_ads * psi2, rtol=1e-13, atol=0)
+    assert np.allclose(F[2][0, 1:-1], 0.5 * G_ads * psi2, rtol=1e-13, atol=0)   # away from the edge
