@@ -272,24 +272,30 @@ void lbm_batch_destroy(lbm_batch* batch);
 const char* lbm_batch_last_error(const lbm_batch* batch);
 
 /* Totals without allocation.  The paper has no counterpart: this is a service
- * for callers that must not allocate device memory while they run (code being
- * recorded into a CUDA graph, hosts whose device memory is pre-budgeted by their
- * own allocator, real-time loops that cannot block on cudaMalloc/cudaFree).
+ * for callers that cannot allocate device memory while they run -- hosts whose
+ * device memory is handed out up front by their own pool allocator (a
+ * cudaMalloc from inside them would go around that budget) and real-time loops
+ * that may not block on cudaMalloc / cudaFree, which can synchronise the device.
  * Computes, in FP64 and in a fixed order (deterministic), totals[0] = sum rho,
  * totals[1..3] = sum rho u_x, sum rho u_y, sum rho u_z over ncell cells of
- * caller-held DEVICE arrays rho (ncell floats) and u (3 ncell floats, the
- * layout lbm_get_moments writes); totals is a DEVICE pointer to 4 doubles.
- * Enqueued on cuda_stream (NULL = legacy default stream); does not wait.
+ * caller-held arrays rho (ncell floats) and u (3 ncell floats, the layout
+ * lbm_get_moments writes) in memory of the current device; totals is a pointer
+ * to 4 doubles in memory of the current device.  Pointers that are NULL, not
+ * naturally aligned, or not device / managed memory of the current device are
+ * refused with LBM_ERR_ARG before any launch.  Enqueued on cuda_stream
+ * (NULL = legacy default stream); does not wait.
  * It calls no cudaMalloc / cudaFree: its scratch (one partial sum per block)
  * is a fixed 512 KB device array in the library that every GPU loading the
  * library holds until the process exits, so ncell is limited to
- * LBM_NOALLOC_MAX_CELLS; larger ncell (or ncell < 1, or a NULL pointer) returns
- * LBM_ERR_ARG with a message in lbm_last_error(NULL).  The first call on a
- * device looks up the array's device address (once per device, with that device
- * current); make that first call before any stream capture.  All calls on one
- * device share the array: calls that may overlap on that GPU (e.g. on two
- * streams) race; serialise them.  The partials are rewritten by every call, so
- * no state carries over between calls. */
+ * LBM_NOALLOC_MAX_CELLS; larger ncell (or ncell < 1) returns LBM_ERR_ARG with a
+ * message in lbm_last_error(NULL).  The first call on a device looks up the
+ * array's device address (once per device, with that device current) and keeps
+ * it for the life of the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) after that first call is not
+ * supported: the kept address would be stale.  All calls on one device share
+ * the array: calls that may overlap on that GPU (e.g. on two streams) race;
+ * serialise them.  The partials are rewritten by every call, so no state
+ * carries over between calls. */
 #define LBM_NOALLOC_MAX_CELLS 33554432
 lbm_status lbm_field_totals_noalloc(const float* rho, const float* u, int64_t ncell, double* totals,
                                     void* cuda_stream);

@@ -1,11 +1,11 @@
 // lbm_field_totals_noalloc: FP64 totals of caller-held rho / u fields without any allocation.
 //
-// Who needs this: callers that must not allocate device memory while they run -- code being
-// recorded into a CUDA graph (an allocation would break or serialise the capture), host
-// applications whose device memory is pre-budgeted by their own allocator, and real-time loops
-// that may not block on cudaMalloc / cudaFree.  They bring their own input and output buffers;
-// the only scratch this path needs (one partial sum per block) lives in a fixed device array
-// declared below, which every GPU that loads the library holds until the process exits.
+// Who needs this: callers that cannot allocate device memory while they run -- host applications
+// whose device memory is handed out up front by their own pool allocator (a cudaMalloc from inside
+// them would go around their budget), and real-time loops that may not block on cudaMalloc /
+// cudaFree, which can synchronise the whole device.  They bring their own input and output
+// buffers; the only scratch this path needs (one partial sum per block) lives in a fixed device
+// array declared below, which every GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,7 +32,10 @@ double* g_partials_addr[NA_MAX_DEVICES] = {};
 std::mutex g_setup_mutex;
 
 // Device address of g_partials on the current device.  In host code the symbol is only a
-// host-side stand-in, so the address is looked up once per device (with that device current).
+// host-side stand-in, so the address is looked up at set-up, once per device, with that device
+// current, and kept for the life of the process.  A cudaDeviceReset destroys the context the
+// address belongs to; the cached address is then stale, so this entry point does not support a
+// device reset in the same process.
 cudaError_t partials_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -47,6 +50,20 @@ cudaError_t partials_address(double** out) {
     }
     *out = g_partials_addr[dev];
     return cudaSuccess;
+}
+
+// True when p is memory of the current device (device or managed allocation) aligned to `align`
+// bytes.  cudaPointerGetAttributes allocates nothing; a plain host pointer reports
+// cudaMemoryTypeUnregistered (or an error, which is cleared) and is refused.
+bool on_current_device(const void* p, size_t align, int dev) {
+    if (!p || (reinterpret_cast<uintptr_t>(p) % align) != 0) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    return a.type == cudaMemoryTypeManaged || a.device == dev;
 }
 
 // Per-block partial sums in a fixed order: each thread adds its cells in index order, then a
@@ -106,6 +123,17 @@ extern "C" lbm_status lbm_field_totals_noalloc(const float* rho, const float* u,
                                                void* cuda_stream) {
     if (!rho || !u || !totals) {
         lbm::set_thread_error("lbm_field_totals_noalloc: rho, u and totals must be device pointers");
+        return LBM_ERR_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        lbm::set_thread_error("lbm_field_totals_noalloc: no current CUDA device");
+        return LBM_ERR_CUDA;
+    }
+    if (!on_current_device(rho, alignof(float), dev) || !on_current_device(u, alignof(float), dev) ||
+        !on_current_device(totals, alignof(double), dev)) {
+        lbm::set_thread_error("lbm_field_totals_noalloc: rho and u must be float arrays and totals a double array "
+                              "in memory of the current device (device or managed allocations), naturally aligned");
         return LBM_ERR_ARG;
     }
     if (ncell < 1 || ncell > (int64_t)LBM_NOALLOC_MAX_CELLS) {

@@ -155,10 +155,24 @@ class Params:
 def field_totals_noalloc(rho, u, totals, stream=None):
     """lbm_field_totals_noalloc: FP64 (sum rho, sum rho u_x, sum rho u_y, sum rho u_z) of caller-held
     CUDA tensors rho (n floats) and u (3 n floats) into the caller's CUDA tensor `totals` (4 doubles),
-    enqueued on `stream`.  For callers that must not allocate device memory while they run (graph
-    capture, pre-budgeted allocators, real-time loops): the library uses a fixed scratch array instead
-    of cudaMalloc, so n is limited to LBM_NOALLOC_MAX_CELLS = 33554432 and calls that overlap on one
-    GPU race.  Make the first call on a device before any stream capture."""
+    enqueued on `stream`.  For callers that cannot allocate device memory while they run (a
+    pre-budgeted pool allocator, a real-time loop that may not block on cudaMalloc): the library uses
+    a fixed scratch array instead of cudaMalloc, so n is limited to LBM_NOALLOC_MAX_CELLS = 33554432
+    and calls that overlap on one GPU race.  The first call on a device sets up the scratch address;
+    make it before any stream capture.  All three tensors must be contiguous and on the current CUDA
+    device, rho and u float32, totals float64 (ValueError otherwise; nothing is converted or copied,
+    since a copy would allocate)."""
+    torch = _torch()
+    for name, t, dt in (("rho", rho, torch.float32), ("u", u, torch.float32), ("totals", totals, torch.float64)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device (cuda:{torch.cuda.current_device()}), "
+                             f"got {t.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
     L = lib()
     n = int(rho.numel())
     if int(u.numel()) != 3 * n or int(totals.numel()) != 4:
