@@ -34,8 +34,9 @@ import workloads as W  # noqa: E402
 METRIC = "MLUPS & % HBM peak (fused MRT-pseudopotential step); batched p50/p99 job latency"
 UNIT = "MLUPS"
 SHAPE = (256, 256, 256)
-WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (0.5Tc leaves the EOS range within 100 steps "
-            "at this droplet size, in the FP64 oracle as on the GPU), Maxwell coexistence densities (ratio 132), "
+WORKLOAD = ("256^3 periodic, C-S EOS (a=0.5,b=4,R=1) at T=0.6Tc (at 0.5Tc the start-up pressure wave compresses "
+            "the centre of the smallest droplet past the C-S range within 20 steps), Maxwell coexistence "
+            "densities (ratio 132), "
             "random sphere droplets r~U[10,40] (seed 2306, liquid fraction>=0.10, tanh W=3), kappa=0.5, "
             "sigma=0.1, G=-1, the paper's default rates, FP32 populations (AA in place)")
 
@@ -327,6 +328,7 @@ def run_batched(steps, n_jobs=64):
         batch_ms = e0.elapsed_time(e1)
         batch.sync()
         info = batch.info()
+        shapes = [g["shape"] for g in batch.groups()]
         batch.close()
         for s in sims:
             s.close()
@@ -337,12 +339,14 @@ def run_batched(steps, n_jobs=64):
             "batched": {"mlups": cells * steps / (batch_ms * 1e-3) / 1e6, "ms": batch_ms,
                         "hbm_frac": byts * steps / (batch_ms * 1e-3) / 1e9 / measured_peaks()[0],
                         "groups": info["groups"], "tiles": info["tiles"], "graph_mode": info["graph_mode"],
-                        "zchunk": choice, "launches_per_step": 2 * info["groups"]},
+                        "zchunk": choice, "tile_shapes": shapes, "launches_per_step": 2 * info["groups"]},
             "speedup": loop_ms / batch_ms}
 
 
 # ---------------------------------------------------------------- serving (continuous batching)
-SERVE_WORKLOAD = ("request stream of {n} jobs (numpy seed 2306): by fair coin droplet impact on a wall with a cylinder "
+SERVE_WORKLOAD = ("request stream of {n} jobs (numpy seed 2306; scheduler under Poisson arrivals: aged shortest-remaining-"
+                  "work first, alpha = {alpha} s/s, {k} jobs per tick; all resident jobs per tick when all arrive at "
+                  "once): by fair coin droplet impact on a wall with a cylinder "
                   "(Sec. IV B; edge L ~ U{{64..160}}, R0 = L/6, R/R0 ~ U[0.2, 2], cylinder on the bottom wall along y, "
                   "walls in z, G_ads = 0.23, We = 10 from the oracle's Laplace surface tension, nu = 0.05, tanh width 3, "
                   "run until "
@@ -351,9 +355,12 @@ SERVE_WORKLOAD = ("request stream of {n} jobs (numpy seed 2306): by fair coin dr
                   "C-S at 0.7 T_c, sigma = 0.1; ticks of 100 steps; budget 150 GB")
 
 
+_FIELDS = {}
+
+
 def serving_specs(n_jobs, rate, seed=2306):
     """JobSpecs of the serving workload, arrivals Poisson with `rate` per second (0: all at once).
-    Fields are generated once here (the client's side of a request) and handed over as float32."""
+    Fields are generated once per job (the client's side of a request) and handed over as float32."""
     from paper_2306_16274_gb300 import Params
     from paper_2306_16274_gb300.serve import JobSpec
     c = W.constants()["cs"]
@@ -369,31 +376,41 @@ def serving_specs(n_jobs, rate, seed=2306):
             tau = (rl * R0 ** 3 / gamma) ** 0.5              # capillary time of Sec. III E
             p = Params(lattice=j["lattice"], shape=j["shape"], bc=("periodic", "periodic", "wall"), kappa=0.3,
                        G_ads=0.23, rates={"s2": 1.0 / (3 * 0.05 + 0.5)}, **eos)
-            rho, u, solid = W.cylinder_impact(j["shape"], R0, j["Rc"], rl, rv, U, gap=3.0, W=3.0)
-            f = (rho.astype(np.float32), u.astype(np.float32), solid)
+            if j["name"] not in _FIELDS:
+                rho, u, solid = W.cylinder_impact(j["shape"], R0, j["Rc"], rl, rv, U, gap=3.0, W=3.0)
+                _FIELDS[j["name"]] = (rho.astype(np.float32), u.astype(np.float32), solid)
+            f = _FIELDS[j["name"]]
             specs.append(JobSpec(name=j["name"], params=p, make_fields=lambda f=f: f, steps=int(4 * tau),
                                  stop_on_detach=True, threshold=0.5 * (rl + rv), arrival=j["arrival"],
                                  has_solid=True, detach_hold=int(0.3 * tau)))
         else:
             p = Params(lattice=j["lattice"], shape=j["shape"], kappa=0.15 * (k % 5), **eos)
-            rho, u = W.droplet(j["shape"], j["R"], rl, rv)
-            f = (rho.astype(np.float32), u.astype(np.float32), None)
+            if j["name"] not in _FIELDS:
+                rho, u = W.droplet(j["shape"], j["R"], rl, rv)
+                _FIELDS[j["name"]] = (rho.astype(np.float32), u.astype(np.float32), None)
+            f = _FIELDS[j["name"]]
             specs.append(JobSpec(name=j["name"], params=p, make_fields=lambda f=f: f, steps=2000,
                                  arrival=j["arrival"]))
     return specs
 
 
-def run_serving(n_jobs=24, load=0.8, tick=100, budget=150e9):
-    """The request stream served one job at a time (single-domain kernels) and with continuous
-    batching: first all requests at t = 0 (throughput), then Poisson arrivals at `load` times the
-    one-at-a-time service rate measured in the first run (time-to-result)."""
+SERVE_ALPHA, SERVE_BATCH = 1.0, 2
+
+
+def run_serving(n_jobs=64, load=0.8, tick=100, budget=150e9):
+    """The request stream served one job at a time (single-domain kernels, first come first served)
+    and with continuous batching: first all requests at t = 0, every resident job advanced each tick
+    (throughput); then Poisson arrivals at `load` times the one-at-a-time service rate measured in
+    the first run (time-to-result), batched with the aged shortest-remaining-work scheduler, and for
+    context with every resident job advanced each tick."""
     import torch
 
     from paper_2306_16274_gb300.serve import GpuEngine, Server, summary
 
-    def serve(specs, batched):
+    def serve(specs, batched, policy="all"):
         eng = GpuEngine(batched=batched)
-        srv = Server(eng, budget, tick=tick, max_active=64 if batched else 1)
+        srv = Server(eng, budget, tick=tick, max_active=64 if batched else 1, policy=policy, alpha=SERVE_ALPHA,
+                     max_batch=SERVE_BATCH)
         res = srv.run(specs)
         eng.close()
         torch.cuda.synchronize()
@@ -401,26 +418,33 @@ def run_serving(n_jobs=24, load=0.8, tick=100, budget=150e9):
         out["failed"] = [r.name + ": " + r.status for r in res if r.status != "ok"]
         return out, res
 
+    def same(ra, rb):
+        return all(a.steps == b.steps and a.touch == b.touch and a.detach == b.detach and a.sums == b.sums
+                   for a, b in zip(ra, rb))
+
     closed = serving_specs(n_jobs, 0.0)
     seq_c, seq_res = serve(closed, False)
     bat_c, bat_res = serve(closed, True)
-    same = all(a.steps == b.steps and a.touch == b.touch and a.detach == b.detach and a.sums == b.sums
-               for a, b in zip(seq_res, bat_res))
     rate = load * n_jobs / seq_c["busy_s"]
     open_ = serving_specs(n_jobs, rate)
     seq_o, _ = serve(open_, False)
-    bat_o, _ = serve(open_, True)
+    bat_o, bat_o_res = serve(open_, True, "aged_srpt")
+    all_o, _ = serve(open_, True)
     keep = ("p50_s", "p99_s", "mean_s", "wall_s", "busy_s", "mlups_busy", "mlups_wall", "peak_active", "peak_bytes",
             "ok", "failed")
     tc = [r.contact_steps for r in bat_res if r.contact_steps is not None]
-    return {"workload": SERVE_WORKLOAD.format(n=n_jobs), "jobs": n_jobs, "cell_steps": seq_c["cell_steps"],
-            "results_equal_alone_and_batched": same,
+    return {"workload": SERVE_WORKLOAD.format(n=n_jobs, alpha=SERVE_ALPHA, k=SERVE_BATCH), "jobs": n_jobs,
+            "cell_steps": seq_c["cell_steps"],
+            "results_equal_alone_and_batched": same(seq_res, bat_res) and same(seq_res, bat_o_res),
             "all_at_once": {"one_at_a_time": {k: seq_c[k] for k in keep},
                             "batched": {k: bat_c[k] for k in keep},
                             "mlups_ratio": bat_c["mlups_wall"] / seq_c["mlups_wall"]},
             "poisson": {"rate_per_s": rate, "load": load,
                         "one_at_a_time": {k: seq_o[k] for k in keep}, "batched": {k: bat_o[k] for k in keep},
-                        "p50_ratio": seq_o["p50_s"] / bat_o["p50_s"], "p99_ratio": seq_o["p99_s"] / bat_o["p99_s"]},
+                        "policy": f"aged_srpt alpha={SERVE_ALPHA} max_batch={SERVE_BATCH}",
+                        "p50_ratio": seq_o["p50_s"] / bat_o["p50_s"], "p99_ratio": seq_o["p99_s"] / bat_o["p99_s"],
+                        "mlups_busy_ratio": bat_o["mlups_busy"] / seq_o["mlups_busy"],
+                        "batched_all_resident": {k: all_o[k] for k in keep}},
             "impacts_detached": len(tc)}
 
 
@@ -555,7 +579,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-onepass", action="store_true")
-    ap.add_argument("--serving-jobs", type=int, default=24)
+    ap.add_argument("--serving-jobs", type=int, default=64)
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
@@ -674,6 +698,7 @@ def main():
             # the metric's second part: time-to-result of the request stream under Poisson arrivals
             line["job_latency"] = {
                 "unit": "s", "arrivals": "Poisson at 0.8 of the one-at-a-time service rate",
+                "scheduler": po.get("policy"),
                 "batched": {"p50": po["batched"]["p50_s"], "p99": po["batched"]["p99_s"],
                             "mean": po["batched"]["mean_s"]},
                 "one_at_a_time": {"p50": po["one_at_a_time"]["p50_s"], "p99": po["one_at_a_time"]["p99_s"],

@@ -126,7 +126,16 @@ typedef struct {
                             /* for bit, twice the population memory.  Periodic boundaries,   */
                             /* no solid mask, FP32 store; cannot join a batch.  0: the       */
                             /* in-place two-pass step (default).                             */
+    int32_t store_layout;   /* FP16 store only.  LBM_LAYOUT_AUTO (0, default): when nx is    */
+                            /* even, x is periodic and no solid mask is given, one 4-byte    */
+                            /* word holds the slots of cells x and x + nx/2 and each thread  */
+                            /* updates both (x-paired layout); otherwise one slot per cell.  */
+                            /* LBM_LAYOUT_SINGLE (1): always one slot per cell.  Results are */
+                            /* the same bit for bit; the layout changes speed only.          */
 } lbm_params;
+
+#define LBM_LAYOUT_AUTO 0
+#define LBM_LAYOUT_SINGLE 1
 
 /* Fills *p with the paper's defaults: D3Q19, 32^3 periodic, no EOS, G = -1,
  * s0 = s1 = 1, s2b = s3b = 0.6, others 1.2 (text after Eq. e12), sigma = 0.1
@@ -232,7 +241,8 @@ void lbm_destroy(lbm_ctx* ctx);
 /* ---------------------------------------------------------------- batches
  * Many independent domains advanced together (the paper's method applied to a set
  * of jobs; the paper itself runs one domain at a time).  Every member is cut into
- * tiles of 32 x 4 columns and runs of z planes; a tile whose cells have no solid
+ * tiles (32 x 4 columns by default, see LBM_BATCH_SHAPES) and runs of z planes; a
+ * tile whose cells have no solid
  * neighbour (mask or wall) goes to a group without solid handling.  Groups are
  * keyed by (lattice, solid handling, physical parameters); each time step costs,
  * per group and per 64 members, one collide-stream launch and one density/psi
@@ -256,18 +266,39 @@ void lbm_destroy(lbm_ctx* ctx);
  * lbm_batch_step: enqueues n >= 0 steps of every member (does not wait) and
  *   advances their step counters.  LBM_ERR_STATE if members were stepped apart.
  * lbm_batch_sync: waits and returns the first sticky member error (lbm_sync).
- * lbm_batch_tune: times the collide launches of every group for trial_steps steps
- *   with each candidate z-chunk (automatic, 1, 2, 4, 8, 16, 32 planes per block),
- *   keeps the fastest per group and writes it to zchunk_out[g] for g < max_groups
- *   (0 = automatic).  The members advance by 7 x (trial_steps + 1) steps.
+ * lbm_batch_tune: autotunes each group's launch shape on the live state, in two
+ *   stages, by timing the collide launches of every group for trial_steps steps:
+ *   first every tile shape (LBM_BATCH_SHAPES) with automatic z-chunks, then, for
+ *   the fastest shape, each candidate z-chunk (automatic, 1, 2, 4, 8, 16, 32
+ *   planes per block).  A group and the group of the same lattice and physics
+ *   with the other solid handling share members, so they take one shape (the
+ *   one with the least summed time); the z-chunk is per group.  Keeps the
+ *   fastest per group and writes its z-chunk to
+ *   zchunk_out[g] for g < max_groups (0 = automatic; lbm_batch_group reads the
+ *   shape).  The members advance by 12 x (trial_steps + 1) steps.
  * lbm_batch_info: number of groups, tiles of all launches of one pass, graph mode
- *   (0 not recorded yet, 1 device-side WHILE loop, 2 replayed two-step graph). */
+ *   (0 not recorded yet, 1 device-side WHILE loop, 2 replayed two-step graph).
+ * lbm_batch_group: lattice (19 | 27), solid handling (0 | 1), tile shape and
+ *   z-chunk of group `group` in [0, ngroups); NULL outputs are skipped.
+ * lbm_batch_set_group: sets a group's tile shape (0 .. LBM_BATCH_SHAPES - 1) and
+ *   z-chunk (0 = automatic) and re-tiles it; the group of the same lattice and
+ *   physics with the other solid handling takes the same shape.  Results do not
+ *   depend on either.
+ *   LBM_ERR_ARG for an unknown group, shape or a negative z-chunk.
+ * Tile shapes (width x height in cells; resident blocks per SM on D3Q19 / D3Q27):
+ *   0: 32 x 4 (7 / 5), the single-domain kernels' shape; 1: 32 x 2 (14 / 10);
+ *   2: 16 x 8 (7 / 5); 3: 16 x 4 (14 / 10); 4: 32 x 4 (6 / 4).  16-wide tiles
+ *   waste fewer threads on domains whose x extent is not a multiple of 32. */
+#define LBM_BATCH_SHAPES 5
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int32_t n, void* cuda_stream, lbm_batch** out);
 lbm_status lbm_batch_step(lbm_batch* batch, int32_t n);
 lbm_status lbm_batch_sync(lbm_batch* batch);
 lbm_status lbm_batch_tune(lbm_batch* batch, int32_t trial_steps, int32_t* zchunk_out, int32_t max_groups);
 lbm_status lbm_batch_info(const lbm_batch* batch, int32_t* ngroups, int32_t* ntiles, int32_t* graph_mode);
+lbm_status lbm_batch_group(const lbm_batch* batch, int32_t group, int32_t* lattice, int32_t* solids, int32_t* shape,
+                           int32_t* zchunk);
+lbm_status lbm_batch_set_group(lbm_batch* batch, int32_t group, int32_t shape, int32_t zchunk);
 void lbm_batch_destroy(lbm_batch* batch);
 const char* lbm_batch_last_error(const lbm_batch* batch);
 

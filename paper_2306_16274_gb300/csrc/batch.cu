@@ -27,8 +27,6 @@ using lbm::KParams;
 
 namespace {
 
-constexpr int PSI_TILE_H = 4;   // rows of the density/psi tiles (its blocks are 32 x 4 threads)
-
 // One launch of a group: up to BATCH_LAUNCH_DOMS members and their tile ranges in the group's
 // tile arrays.
 struct Launch {
@@ -41,6 +39,7 @@ struct Group {
     KParams phys{};                 // physical parameters shared by the members (geometry zeroed)
     std::vector<int> members;       // members with tiles in this group
     int zchunk = 0;                 // 0 = automatic
+    int shape = 0;                  // tile shape: index into lbm::BATCH_SHAPES
     std::vector<Launch> launches;
     BatchTile* tiles = nullptr;     // tiles of both passes (device)
     int ntiles = 0;
@@ -67,6 +66,7 @@ KParams physics_of(const KParams& k) {
     for (float*& q : p.gq) q = nullptr;
     p.zchunk = 0;
     p.zlo = p.zhi = 0;
+    p.paired = p.hx = 0;        // storage layout (FP16 only), not physics
     return p;
 }
 
@@ -135,14 +135,13 @@ void drop_graph(lbm_batch* b) {
     b->graph_mode = 0;
 }
 
-constexpr int TILE_W = 32;
 constexpr int ZC_AUTO_MAX = 32;   // automatic z-chunks: longer marches gain little, and in a mix of
                                   // uneven members shorter blocks balance the last wave
 
-// flags[(z * nyb + yb) * nxb + xb] = 1 if a cell of the 32 x th column (xb, yb) in plane z has a
-// solid neighbour or is solid (its neighbour mask is nonzero).
-__global__ void tile_flags_kernel(const uint32_t* __restrict__ nbmask, int nx, int ny, int th, uint8_t* flags) {
-    const int x = blockIdx.x * TILE_W + threadIdx.x, y = blockIdx.y * th + threadIdx.y, z = blockIdx.z;
+// flags[(z * nyb + yb) * nxb + xb] = 1 if a cell of the blockDim.x x blockDim.y column (xb, yb) in
+// plane z has a solid neighbour or is solid (its neighbour mask is nonzero).
+__global__ void tile_flags_kernel(const uint32_t* __restrict__ nbmask, int nx, int ny, uint8_t* flags) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     bool any = false;
     if (x < nx && y < ny) any = nbmask[((long long)z * ny + y) * nx + x] != 0u;
     any = __syncthreads_or(any);
@@ -150,17 +149,20 @@ __global__ void tile_flags_kernel(const uint32_t* __restrict__ nbmask, int nx, i
         flags[((long long)z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = any ? 1 : 0;
 }
 
-// Mask flags of a member (cached on the context until its fields are re-initialised).
-lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int th) {
+// Mask flags of a member for tw x th columns (cached on the context until its fields are
+// re-initialised or another tile shape asks).
+lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int tw, int th) {
     const KParams& k = c->kp;
-    const long long nxb = (k.nx + TILE_W - 1) / TILE_W, nyb = (k.ny + th - 1) / th;
+    const long long nxb = (k.nx + tw - 1) / tw, nyb = (k.ny + th - 1) / th;
     const size_t n = (size_t)(nxb * nyb * k.nz);
-    if (!c->nbmask || c->tile_flags.size() == n) return LBM_OK;
+    if (!c->nbmask || (c->tile_flags.size() == n && c->tile_flags_tw == tw && c->tile_flags_th == th)) return LBM_OK;
     uint8_t* d = nullptr;
     BCK(b, cudaMalloc((void**)&d, n));
     c->tile_flags.assign(n, 1);
-    tile_flags_kernel<<<dim3((unsigned)nxb, (unsigned)nyb, (unsigned)k.nz), dim3(TILE_W, th), 0, b->stream>>>(
-        c->nbmask, k.nx, k.ny, th, d);
+    c->tile_flags_tw = tw;
+    c->tile_flags_th = th;
+    tile_flags_kernel<<<dim3((unsigned)nxb, (unsigned)nyb, (unsigned)k.nz), dim3(tw, th), 0, b->stream>>>(
+        c->nbmask, k.nx, k.ny, d);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->tile_flags.data(), d, n, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -172,7 +174,7 @@ lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int th) {
     return LBM_OK;
 }
 
-// Tiles of the members of a group: 32 x th cells in (x, y) and a run of z planes.  Along every
+// Tiles of the members of a group: tw x th cells in (x, y) (the group's shape) and a run of z planes.  Along every
 // column the planes are split into runs that need solid handling (a cell with a solid neighbour:
 // mask, or the first / last plane, row or column next to a wall) and runs that do not; runs are
 // cut into chunks of at most zc planes, chosen so that the whole group gives a few waves of
@@ -181,13 +183,14 @@ lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int th) {
 // so only cells near solids pay for the solid tests.
 lbm_status build_tiles(lbm_batch* b, Group& g) {
     free_tiles(g);
-    const int th = g.Q == 19 ? lbm::tile_height_q19() : lbm::tile_height_q27();
-    const int resident = g.Q == 19 ? lbm::resident_blocks_q19() : lbm::resident_blocks_q27();
-    if (th != PSI_TILE_H) return bfail(b, LBM_ERR_STATE, "collide and psi tile heights differ");
+    if (g.shape < 0 || g.shape >= lbm::BATCH_NSHAPES) return bfail(b, LBM_ERR_ARG, "unknown tile shape");
+    const lbm::BatchShape& sh = lbm::BATCH_SHAPES[g.shape];
+    const int tw = sh.bx, th = sh.by;
+    const int resident = g.Q == 19 ? sh.minb19 : sh.minb27;
     long long cols = 0;
     for (int d : g.members) {
         const KParams& k = b->members[d]->kp;
-        cols += (long long)((k.nx + TILE_W - 1) / TILE_W) * ((k.ny + th - 1) / th);
+        cols += (long long)((k.nx + tw - 1) / tw) * ((k.ny + th - 1) / th);
     }
     const long long target = 152LL * resident * 4;
     const long long chunks_auto = std::max(1LL, (target + cols - 1) / std::max(cols, 1LL));
@@ -204,7 +207,7 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
         lbm_ctx* c = b->members[g.members[j]];
         const KParams& k = c->kp;
         const bool solid_work = has_solid_work(c);
-        lbm_status fs = member_tile_flags(b, c, th);
+        lbm_status fs = member_tile_flags(b, c, tw, th);
         if (fs != LBM_OK) return fs;
         int zc;
         if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);            // the batch's tuned choice
@@ -213,13 +216,13 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
             const long long ch = std::min<long long>(chunks_auto, k.nz);
             zc = std::min(ZC_AUTO_MAX, (int)((k.nz + ch - 1) / ch));
         }
-        const int nxb = (k.nx + TILE_W - 1) / TILE_W, nyb = (k.ny + th - 1) / th;
+        const int nxb = (k.nx + tw - 1) / tw, nyb = (k.ny + th - 1) / th;
         const int member_t0 = (int)t.size() - L.t0;
         need.resize(k.nz);
         for (int yb = 0; yb < nyb; ++yb)
             for (int xb = 0; xb < nxb; ++xb) {
-                const int x0 = xb * TILE_W, y0 = yb * th;
-                const bool side = (k.wall_x && (x0 == 0 || x0 + TILE_W >= k.nx)) ||
+                const int x0 = xb * tw, y0 = yb * th;
+                const bool side = (k.wall_x && (x0 == 0 || x0 + tw >= k.nx)) ||
                                   (k.wall_y && (y0 == 0 || y0 + th >= k.ny));
                 for (int z = 0; z < k.nz; ++z) {
                     bool s = side || (k.wall_z && (z == 0 || z == k.nz - 1));
@@ -255,8 +258,8 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
 cudaError_t collide_group(const Group& g, int parity, cudaStream_t st) {
     for (const Launch& L : g.launches) {
         const BatchTile* t = g.tiles + L.t0;
-        cudaError_t e = g.Q == 19 ? lbm::launch_collide_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, st)
-                                  : lbm::launch_collide_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, st);
+        cudaError_t e = g.Q == 19 ? lbm::launch_collide_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st)
+                                  : lbm::launch_collide_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -265,9 +268,9 @@ cudaError_t collide_group(const Group& g, int parity, cudaStream_t st) {
 cudaError_t psi_group(const Group& g, int parity, cudaStream_t st) {
     if (!g.phys.multiphase) return cudaSuccess;
     for (const Launch& L : g.launches) {
-        const BatchTile* t = g.tiles + L.t0;   // the collide tiles (32 x 4 columns, same split)
-        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, st)
-                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, st);
+        const BatchTile* t = g.tiles + L.t0;   // the collide tiles (same shape, same split)
+        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st)
+                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -507,22 +510,40 @@ lbm_status lbm_batch_sync(lbm_batch* b) {
     return first;
 }
 
-lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out, int32_t max_groups) {
-    if (!b) return LBM_ERR_ARG;
-    if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "trial_steps must be >= 1");
-    const int cand[] = {0, 1, 2, 4, 8, 16, 32};
-    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+}  // extern "C"
+
+namespace {
+
+// The group with the same lattice and physics and the other solid handling (-1 if none).  A member
+// with solids has its solid-free tiles in one and the others in the other; both must be cut into the
+// same columns (the same tile shape), or their tiles would not partition the member's cells.
+int partner_group(const lbm_batch* b, int k) {
+    const Group& g = b->groups[k];
+    for (int j = 0; j < (int)b->groups.size(); ++j) {
+        const Group& h = b->groups[j];
+        if (j != k && h.Q == g.Q && h.solids != g.solids && std::memcmp(&h.phys, &g.phys, sizeof(KParams)) == 0)
+            return j;
+    }
+    return -1;
+}
+
+// Times every group's collide launches over `trial_steps` steps with each group set to candidate
+// (shape_of(g, ci), zchunk_of(g, ci)) in turn, ci < ncand; times[ci][g] receives the total.  The
+// members advance by ncand x (trial_steps + 1) steps.
+template <class SF, class ZF>
+lbm_status time_candidates(lbm_batch* b, int trial_steps, int ncand, SF shape_of, ZF zchunk_of,
+                           std::vector<std::vector<double>>& times) {
     const size_t G = b->groups.size();
-    std::vector<double> best(G, 1e300);
-    std::vector<int> choice(G, 0);
+    times.assign(ncand, std::vector<double>(G, 0.0));
     std::vector<cudaEvent_t> ev(2 * G * trial_steps);
     for (auto& e : ev) BCK(b, cudaEventCreate(&e));
     lbm_status result = LBM_OK;
-    for (int ci = 0; ci < nc && result == LBM_OK; ++ci) {
-        for (Group& g : b->groups) {
-            g.zchunk = cand[ci];
+    for (int ci = 0; ci < ncand && result == LBM_OK; ++ci) {
+        for (size_t k = 0; k < G && result == LBM_OK; ++k) {
+            Group& g = b->groups[k];
+            g.shape = shape_of((int)k, ci);
+            g.zchunk = zchunk_of((int)k, ci);
             result = build_tiles(b, g);
-            if (result != LBM_OK) break;
         }
         if (result != LBM_OK) break;
         drop_graph(b);
@@ -546,28 +567,96 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out
         }
         advance_members(b, trial_steps + 1);
         for (size_t k = 0; k < G; ++k) {
-            double tot = 0.0;
             for (int s = 0; s < trial_steps; ++s) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev[2 * (s * G + k)], ev[2 * (s * G + k) + 1]);
-                tot += ms;
-            }
-            if (tot < best[k]) {
-                best[k] = tot;
-                choice[k] = cand[ci];
+                times[ci][k] += ms;
             }
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (result != LBM_OK) return result;
-    for (size_t k = 0; k < G; ++k) {
-        b->groups[k].zchunk = choice[k];
+    return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out, int32_t max_groups) {
+    if (!b) return LBM_ERR_ARG;
+    if (trial_steps < 1) return bfail(b, LBM_ERR_ARG, "trial_steps must be >= 1");
+    const int G = (int)b->groups.size();
+    std::vector<std::vector<double>> t;
+    // stage 1: every tile shape (on all groups at once) with automatic z-chunks; a group and its
+    // partner take the shape that minimises their summed time
+    lbm_status r = time_candidates(
+        b, trial_steps, lbm::BATCH_NSHAPES, [](int, int ci) { return ci; }, [](int, int) { return 0; }, t);
+    if (r != LBM_OK) return r;
+    std::vector<int> shape(G, 0), zchunk(G, 0);
+    for (int k = 0; k < G; ++k) {
+        const int p = partner_group(b, k);
+        double best = 1e300;
+        for (int ci = 0; ci < lbm::BATCH_NSHAPES; ++ci) {
+            const double v = t[ci][k] + (p >= 0 ? t[ci][p] : 0.0);
+            if (v < best) {
+                best = v;
+                shape[k] = ci;
+            }
+        }
+    }
+    // stage 2: the z-chunks for the chosen shapes, per group
+    const int zc[] = {0, 1, 2, 4, 8, 16, 32};
+    const int nz = (int)(sizeof(zc) / sizeof(zc[0]));
+    r = time_candidates(
+        b, trial_steps, nz, [&](int k, int) { return shape[k]; }, [&](int, int ci) { return zc[ci]; }, t);
+    if (r != LBM_OK) return r;
+    for (int k = 0; k < G; ++k) {
+        double best = 1e300;
+        for (int ci = 0; ci < nz; ++ci)
+            if (t[ci][k] < best) {
+                best = t[ci][k];
+                zchunk[k] = zc[ci];
+            }
+    }
+    for (int k = 0; k < G; ++k) {
+        b->groups[k].shape = shape[k];
+        b->groups[k].zchunk = zchunk[k];
         lbm_status s = build_tiles(b, b->groups[k]);
         if (s != LBM_OK) return s;
-        if (zchunk_out && (int)k < max_groups) zchunk_out[k] = choice[k];
+        if (zchunk_out && k < max_groups) zchunk_out[k] = zchunk[k];
     }
     drop_graph(b);
     return LBM_OK;
+}
+
+lbm_status lbm_batch_group(const lbm_batch* b, int32_t group, int32_t* lattice, int32_t* solids, int32_t* shape,
+                           int32_t* zchunk) {
+    if (!b) return LBM_ERR_ARG;
+    if (group < 0 || group >= (int32_t)b->groups.size()) return LBM_ERR_ARG;
+    const Group& g = b->groups[group];
+    if (lattice) *lattice = g.Q;
+    if (solids) *solids = g.solids;
+    if (shape) *shape = g.shape;
+    if (zchunk) *zchunk = g.zchunk;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_group(lbm_batch* b, int32_t group, int32_t shape, int32_t zchunk) {
+    if (!b) return LBM_ERR_ARG;
+    if (group < 0 || group >= (int32_t)b->groups.size()) return bfail(b, LBM_ERR_ARG, "no such group");
+    if (shape < 0 || shape >= lbm::BATCH_NSHAPES) return bfail(b, LBM_ERR_ARG, "shape must lie in [0, LBM_BATCH_SHAPES)");
+    if (zchunk < 0) return bfail(b, LBM_ERR_ARG, "zchunk must be >= 0");
+    Group& g = b->groups[group];
+    g.shape = shape;
+    g.zchunk = zchunk;
+    drop_graph(b);
+    lbm_status s = build_tiles(b, g);
+    const int p = partner_group(b, group);
+    if (s == LBM_OK && p >= 0 && b->groups[p].shape != shape) {   // the partner takes the same columns
+        b->groups[p].shape = shape;
+        s = build_tiles(b, b->groups[p]);
+    }
+    return s;
 }
 
 lbm_status lbm_batch_info(const lbm_batch* b, int32_t* ngroups, int32_t* ntiles, int32_t* graph_mode) {

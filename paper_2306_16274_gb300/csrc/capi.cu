@@ -70,6 +70,10 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         return LBM_ERR_ARG;
     }
     if (p->onepass != 0 && p->onepass != 1) { why = "onepass must be 0 or 1"; return LBM_ERR_ARG; }
+    if (p->store_layout != LBM_LAYOUT_AUTO && p->store_layout != LBM_LAYOUT_SINGLE) {
+        why = "store_layout must be LBM_LAYOUT_AUTO or LBM_LAYOUT_SINGLE";
+        return LBM_ERR_ARG;
+    }
     if (p->onepass && (p->store != LBM_STORE_FP32 || p->bc[0] != LBM_BC_PERIODIC || p->bc[1] != LBM_BC_PERIODIC ||
                        p->bc[2] != LBM_BC_PERIODIC)) {
         why = "onepass needs the FP32 store and periodic boundaries on all axes";
@@ -157,6 +161,15 @@ KParams derive(const lbm_params& p, long long plane) {
     return k;
 }
 
+// The shifted FP16 store keeps two cells per 4-byte word (x-paired layout) when nx is even, x is
+// periodic and there is no solid mask; the layout is fixed whenever all slots are rewritten
+// (create, init_fields, set_populations keep it until the next init_fields).
+void set_layout(lbm_ctx* c, bool with_mask) {
+    c->paired = c->f16 && c->p.store_layout == LBM_LAYOUT_AUTO && c->kp.nx % 2 == 0 && !c->kp.wall_x && !with_mask;
+    c->kp.paired = c->paired;
+    c->kp.hx = c->kp.nx / 2;
+}
+
 bool has_solids(const lbm_ctx* c) {
     return c->nbmask != nullptr || c->kp.wall_x || c->kp.wall_y || c->kp.wall_z;
 }
@@ -170,6 +183,7 @@ lbm::Bufs bufs(const lbm_ctx* c) {
     b.nbmask = c->nbmask;
     b.status = c->status;
     b.f16 = c->f16;
+    b.paired = c->paired;
     b.rsrc = c->f16 ? c->rbuf[c->rs] : nullptr;
     b.rnew = c->f16 ? c->rbuf[c->rs ^ 1] : nullptr;
     return b;
@@ -348,6 +362,7 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
     };
     cudaError_t e = cudaGetDevice(&c->device);
     c->f16 = params->store == LBM_STORE_FP16;
+    set_layout(c, false);
     const size_t esize = c->f16 ? 2 : sizeof(float);   // FP16 slots are __half
     if (e == cudaSuccess) e = alloc((void**)&c->f, (size_t)c->Q * plane * esize);
     if (e == cudaSuccess)
@@ -410,6 +425,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const float* rho, const float* u, const u
         c->nbmask = nullptr;
     }
     c->tile_flags.clear();
+    set_layout(c, solid != nullptr);
     if (c->onepass) {
         // natural-order populations into the other copy, then shifted into the pull layout
         lbm::KParams kn = c->kp;

@@ -17,6 +17,7 @@ struct lbm_ctx {
     // device state
     float* f = nullptr;          // Q planes of `plane` slots (AA layout): floats, or __half with f16
     int f16 = 0;                 // shifted FP16 store (LBM_STORE_FP16)
+    int paired = 0;              // f16 slots in the x-paired layout (see KParams::paired)
     int onepass = 0;             // one-pass layout: f is the copy being read, f2 the one written
     float* f2 = nullptr;
     float* rbuf[2] = {nullptr, nullptr};   // f16: density fields, see bufs() in capi.cu
@@ -33,6 +34,7 @@ struct lbm_ctx {
     // per 32 x 4 column and z plane: 1 if some cell there has a solid neighbour (mask only),
     // computed on first use by a multi-domain batch, cleared when the fields are re-initialised
     std::vector<uint8_t> tile_flags;
+    int tile_flags_tw = 0, tile_flags_th = 0;   // the column shape tile_flags was computed for
     // domains with walls or solids step through a one-member batch (created on first use): its
     // tiles away from solids take the kernels without solid handling
     lbm_batch* self_batch = nullptr;

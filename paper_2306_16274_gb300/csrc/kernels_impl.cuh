@@ -18,6 +18,20 @@ constexpr int Q = LBM_Q;
 // ---- density + psi pass (Sec. II A, Sec. II C): one thread per cell, x fastest
 constexpr int PSI_BX = 32, PSI_BY = 4;
 
+// Shape of a tile: BX x BY cells in (x, y), one thread each; the z-marching collide kernels keep a
+// psi ring plane of it with a one-cell halo.  The single-domain kernels use 32 x 4 (ZmTile); the
+// multi-domain kernels any shape of BATCH_SHAPES, chosen per group by lbm_batch_tune.
+template <int BX_, int BY_>
+struct TileShape {
+    static constexpr int BX = BX_, BY = BY_, NT = BX * BY;
+    static constexpr int RX = BX + 2, RY = BY + 2, RP = RX * RY;
+    static constexpr int SLOTS = (RP + NT - 1) / NT;   // ring loads per thread per plane
+};
+template <int S>
+using BatchTileShape = TileShape<BATCH_SHAPES[S].bx, BATCH_SHAPES[S].by>;
+template <int S>
+constexpr int batch_minb() { return LBM_Q == 19 ? BATCH_SHAPES[S].minb19 : BATCH_SHAPES[S].minb27; }
+
 // cells (x, y, z) for z in [z0, z1) of one column: pull the populations (AA phase PARITY),
 // rho = sum f, psi from the equation of state.  F16: the slots hold the shifted FP16 store,
 // read with the densities rsrc they were written with; the new densities go to rdst.
@@ -69,12 +83,12 @@ __global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_kernel(KParams kp, float*
 }
 
 
-// multi-domain density + psi pass: one block per tile of any member of the launch's table;
-// physics by value
-template <int PARITY, bool SOLIDS>
-__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_batch_kernel(const KParams phys,
-                                                                  const __grid_constant__ BatchDomTable tab,
-                                                                  const BatchTile* __restrict__ tiles) {
+// multi-domain density + psi pass: one block per tile (of shape S) of any member of the launch's
+// table; physics by value
+template <int PARITY, bool SOLIDS, int S>
+__global__ void __launch_bounds__(BatchTileShape<S>::NT) psi_batch_kernel(const KParams phys,
+                                                                       const __grid_constant__ BatchDomTable tab,
+                                                                       const BatchTile* __restrict__ tiles) {
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
@@ -103,9 +117,8 @@ constexpr int CS_BX = 32, CS_BY = 4, CS_BZ = 2;        // 3D tile shape of the m
 #define LBM_ZM_MINB27 5
 #endif
 constexpr int ZM_BX = 32, ZM_BY = LBM_ZM_BY, ZM_MINB = LBM_Q == 19 ? LBM_ZM_MINB19 : LBM_ZM_MINB27;
-constexpr int ZM_RX = ZM_BX + 2, ZM_RY = ZM_BY + 2, ZM_RP = ZM_RX * ZM_RY;
-constexpr int ZM_NT = ZM_BX * ZM_BY;
-constexpr int ZM_SLOTS = (ZM_RP + ZM_NT - 1) / ZM_NT;  // psi loads per thread per plane
+
+using ZmTile = TileShape<ZM_BX, ZM_BY>;
 
 // plane offsets of z in a 32-bit neighbourhood
 __device__ __forceinline__ void set_plane(Off32& o, int z, int nz, uint32_t nxy) {
@@ -116,39 +129,42 @@ __device__ __forceinline__ void set_plane(Off32& o, int z, int nz, uint32_t nxy)
 }
 
 // psi plane zz (wrapped, or zeros beyond a wall) into one ring slot; each thread loads its
-// ZM_SLOTS entries, whose x/y offsets are fixed for the whole march.
+// TS::SLOTS entries, whose x/y offsets are fixed for the whole march.
+template <class TS>
 __device__ __forceinline__ void load_psi_plane(float* slot, const float* __restrict__ psi, int zz, int nz, int wall_z,
-                                               uint32_t nxy, const uint32_t (&goff)[ZM_SLOTS],
-                                               const bool (&gok)[ZM_SLOTS], int tid) {
+                                               uint32_t nxy, const uint32_t (&goff)[TS::SLOTS],
+                                               const bool (&gok)[TS::SLOTS], int tid) {
     bool zok = true;
     if (zz < 0) { zok = !wall_z; zz += nz; } else if (zz >= nz) { zok = !wall_z; zz -= nz; }
     const uint32_t zb = (uint32_t)zz * nxy;
 #pragma unroll
-    for (int s = 0; s < ZM_SLOTS; ++s) {
-        const int k = tid + s * ZM_NT;
-        if (k < ZM_RP) slot[k] = (zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
+    for (int s = 0; s < TS::SLOTS; ++s) {
+        const int k = tid + s * TS::NT;
+        if (k < TS::RP) slot[k] = (zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
     }
 }
 
 // the same plane in two halves: the loads into registers, then (an iteration later) the stores
 // into the ring slot, so that the loads' latency is spent on a plane's collision
-__device__ __forceinline__ void fetch_psi_plane(float (&v)[ZM_SLOTS], const float* __restrict__ psi, int zz, int nz,
-                                                int wall_z, uint32_t nxy, const uint32_t (&goff)[ZM_SLOTS],
-                                                const bool (&gok)[ZM_SLOTS], int tid) {
+template <class TS>
+__device__ __forceinline__ void fetch_psi_plane(float (&v)[TS::SLOTS], const float* __restrict__ psi, int zz, int nz,
+                                                int wall_z, uint32_t nxy, const uint32_t (&goff)[TS::SLOTS],
+                                                const bool (&gok)[TS::SLOTS], int tid) {
     bool zok = true;
     if (zz < 0) { zok = !wall_z; zz += nz; } else if (zz >= nz) { zok = !wall_z; zz -= nz; }
     const uint32_t zb = (uint32_t)zz * nxy;
 #pragma unroll
-    for (int s = 0; s < ZM_SLOTS; ++s) {
-        const int k = tid + s * ZM_NT;
-        v[s] = (k < ZM_RP && zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
+    for (int s = 0; s < TS::SLOTS; ++s) {
+        const int k = tid + s * TS::NT;
+        v[s] = (k < TS::RP && zok && gok[s]) ? __ldg(psi + bounded(zb + goff[s], (unsigned long long)nxy * nz)) : 0.0f;
     }
 }
-__device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_SLOTS], int tid) {
+template <class TS>
+__device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[TS::SLOTS], int tid) {
 #pragma unroll
-    for (int s = 0; s < ZM_SLOTS; ++s) {
-        const int k = tid + s * ZM_NT;
-        if (k < ZM_RP) slot[k] = v[s];
+    for (int s = 0; s < TS::SLOTS; ++s) {
+        const int k = tid + s * TS::NT;
+        if (k < TS::RP) slot[k] = v[s];
     }
 }
 
@@ -156,32 +172,32 @@ __device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[ZM_S
 #define LBM_ZM_PREFETCH 1
 #endif
 
-// One tile: cells [x0, x0+32) x [y0, y0+ZM_BY) marching through planes [z0, z0+zchunk); `addr`
+// One tile: cells [x0, x0+TS::BX) x [y0, y0+TS::BY) marching through planes [z0, z0+zchunk); `addr`
 // locates population planes.  F16 (shifted FP16 store): the densities the slots were written
 // with (rsrc) follow the march in a second shared ring `rring`; outputs are written relative
 // to the cell's current density rown.
 // PSI_PF: the psi (and FP16 density) ring planes are loaded into registers one plane ahead and
 // stored into the ring at the next plane (all but the multi-domain kernels' solid tiles, which
 // have no registers to spare and load each plane just before its barrier).
-template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
+template <class TS, int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
-                                             int z0, int zchunk, int zmax, float (*ring)[ZM_RP], float (*rring)[ZM_RP],
+                                             int z0, int zchunk, int zmax, float (*ring)[TS::RP], float (*rring)[TS::RP],
                                              const float* __restrict__ rsrc, const float* __restrict__ rown) {
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ZM_BX * ty;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TS::BX * ty;
     const int x = x0 + tx, y = y0 + ty;
     const int nx = g.nx(), ny = g.ny(), nz = g.nz();
     const bool act_xy = x < nx && y < ny;
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
     const int zend = min(z0 + zchunk, zmax);
 
-    uint32_t goff[ZM_SLOTS];
-    bool gok[ZM_SLOTS];
+    uint32_t goff[TS::SLOTS];
+    bool gok[TS::SLOTS];
 #pragma unroll
-    for (int s = 0; s < ZM_SLOTS; ++s) {
-        const int k = tid + s * ZM_NT;
-        int gx = x0 - 1 + k % ZM_RX, gy = y0 - 1 + k / ZM_RX;
-        bool ok = k < ZM_RP;
+    for (int s = 0; s < TS::SLOTS; ++s) {
+        const int k = tid + s * TS::NT;
+        int gx = x0 - 1 + k % TS::RX, gy = y0 - 1 + k / TS::RX;
+        bool ok = k < TS::RP;
         if (gx < 0) { ok &= !g.wall_x(); gx += nx; } else if (gx >= nx) { ok &= !g.wall_x(); gx -= nx; }
         if (gy < 0) { ok &= !g.wall_y(); gy += ny; } else if (gy >= ny) { ok &= !g.wall_y(); gy -= ny; }
         ok = ok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
@@ -209,31 +225,31 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         if (!(bits_n & 1u)) gather32<Q, PARITY, SOLIDS>(addr, o, bits_n, pn);
     }
 #endif
-    float pv[ZM_SLOTS], rv[ZM_SLOTS];
-    if (PSI_PF && MULTIPHASE) fetch_psi_plane(pv, psi, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
-    if (PSI_PF && F16) fetch_psi_plane(rv, rsrc, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+    float pv[TS::SLOTS], rv[TS::SLOTS];
+    if (PSI_PF && MULTIPHASE) fetch_psi_plane<TS>(pv, psi, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+    if (PSI_PF && F16) fetch_psi_plane<TS>(rv, rsrc, z0 + 1, nz, g.wall_z(), nxy, goff, gok, tid);
     if (MULTIPHASE) {
-        load_psi_plane(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
-        load_psi_plane(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane<TS>(ring[0], psi, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane<TS>(ring[1], psi, z0, nz, g.wall_z(), nxy, goff, gok, tid);
     }
     if (F16) {
-        load_psi_plane(rring[0], rsrc, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
-        load_psi_plane(rring[1], rsrc, z0, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane<TS>(rring[0], rsrc, z0 - 1, nz, g.wall_z(), nxy, goff, gok, tid);
+        load_psi_plane<TS>(rring[1], rsrc, z0, nz, g.wall_z(), nxy, goff, gok, tid);
     }
-    const int lc = (ty + 1) * ZM_RX + tx + 1;   // this cell's position in a ring plane
+    const int lc = (ty + 1) * TS::RX + tx + 1;   // this cell's position in a ring plane
     for (int z = z0, j = 0; z < zend; ++z, ++j) {
         if (PSI_PF) {
             if (MULTIPHASE) {
-                put_psi_plane(ring[(j + 2) & 3], pv, tid);
-                if (z + 1 < zend) fetch_psi_plane(pv, psi, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
+                put_psi_plane<TS>(ring[(j + 2) & 3], pv, tid);
+                if (z + 1 < zend) fetch_psi_plane<TS>(pv, psi, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
             }
             if (F16) {
-                put_psi_plane(rring[(j + 2) & 3], rv, tid);
-                if (z + 1 < zend) fetch_psi_plane(rv, rsrc, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
+                put_psi_plane<TS>(rring[(j + 2) & 3], rv, tid);
+                if (z + 1 < zend) fetch_psi_plane<TS>(rv, rsrc, z + 2, nz, g.wall_z(), nxy, goff, gok, tid);
             }
         } else {
-            if (MULTIPHASE) load_psi_plane(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
-            if (F16) load_psi_plane(rring[(j + 2) & 3], rsrc, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+            if (MULTIPHASE) load_psi_plane<TS>(ring[(j + 2) & 3], psi, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
+            if (F16) load_psi_plane<TS>(rring[(j + 2) & 3], rsrc, z + 1, nz, g.wall_z(), nxy, goff, gok, tid);
         }
         if (MULTIPHASE || F16) __syncthreads();
         if (!act_xy) continue;
@@ -257,11 +273,11 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
         gather32<Q, PARITY, SOLIDS>(addr, o, bits, p);
 #endif
         if (F16) denorm<Q, SOLIDS>(p, bits, RsRing{&rring[j & 3][lc], &rring[(j + 1) & 3][lc],
-                                                    &rring[(j + 2) & 3][lc], ZM_RX});
+                                                    &rring[(j + 2) & 3][lc], TS::RX});
         Forces Fo;
         if (MULTIPHASE) {
             Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][lc], &ring[(j + 1) & 3][lc], &ring[(j + 2) & 3][lc],
-                                            ZM_RX, bits);
+                                            TS::RX, bits);
         } else {
             Fo.fx = Fo.fy = Fo.fz = 0.f;
             Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
@@ -276,17 +292,336 @@ __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, con
 }
 
 template <int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16>
-__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
+__global__ void __launch_bounds__(ZmTile::NT, ZM_MINB) collide_kernel(const KParams kp, const float* __restrict__ psi,
                                                                 const uint32_t* __restrict__ nbmask,
                                                                 unsigned* status, int zchunk,
                                                                 const float* __restrict__ rsrc,
                                                                 const float* __restrict__ rown) {
-    __shared__ float ring[F16 ? 8 : 4][ZM_RP];
+    __shared__ float ring[F16 ? 8 : 4][ZmTile::RP];
     const KGeom g{kp};
     const PlanePtrsT<typename std::conditional<F16, __half, float>::type> addr{kp};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE, F16, true>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
+    collide_tile<ZmTile, PARITY, SOLIDS, MULTIPHASE, F16, true>(kp, g, addr, psi, nbmask, status, blockIdx.x * ZM_BX,
                                                         blockIdx.y * ZM_BY, kp.zlo + (int)blockIdx.z * zchunk,
                                                         zchunk, kp.zhi, ring, ring + 4, rsrc, rown);
+}
+
+// ---- shifted FP16 store in the x-paired layout (KParams::paired: even nx, x periodic, no solid
+// mask).  One thread per word, i.e. per cell pair (w, y, z) and (w + hx, y, z); every population
+// slot is read and written as one half2 word, and the two cells share the address arithmetic.  A
+// shift by one cell in x moves a word to the neighbouring word, with its two halves exchanged
+// where the shift wraps around the row (w = 0 to the left, w = hx - 1 to the right).  Per cell
+// the arithmetic and its order are those of the one-cell kernels above, so both layouts give the
+// same populations bit for bit.
+
+// word offsets of a pair's neighbourhood within a population plane (ncell / 2 words)
+struct WOff {
+    uint32_t c;
+    uint32_t wo[3];   // words w-1, w, w+1 wrapped in [0, hx)
+    uint32_t yo[3];   // rows y-1, y, y+1 wrapped, times hx
+    uint32_t zo[3];   // planes z-1, z, z+1 wrapped, times ny hx
+    __device__ __forceinline__ uint32_t nb(int dx, int dy, int dz) const { return zo[dz + 1] + yo[dy + 1] + wo[dx + 1]; }
+};
+
+__device__ __forceinline__ void set_wplane(WOff& o, int z, int nz, uint32_t wpl) {
+    o.zo[0] = (uint32_t)wrap1(z - 1, nz) * wpl;
+    o.zo[1] = (uint32_t)z * wpl;
+    o.zo[2] = (uint32_t)wrap1(z + 1, nz) * wpl;
+    o.c = o.zo[1] + o.yo[1] + o.wo[1];
+}
+
+struct WordPlanes {
+    const KParams& kp;
+    __device__ __forceinline__ uint32_t* ptr(int i, uint32_t off) const {
+#if LBM_BOUNDS_CHECK
+        if (i < 0 || i >= 27 || !kp.fq[i]) {
+            atomicAdd(&lbm_bounds_count, 1ull);
+            i = 0;
+        }
+#endif
+        return reinterpret_cast<uint32_t*>(kp.fq[i]) + bounded(off, (unsigned long long)(kp.ncell / 2));
+    }
+};
+
+constexpr uint32_t PERM_KEEP = 0x3210u, PERM_SWAP = 0x1032u;   // __byte_perm selectors: halves kept / exchanged
+
+__device__ __forceinline__ float half_lo(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
+__device__ __forceinline__ float half_hi(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
+
+// AA gather of a pair's slot words (the paired counterpart of gather32); selL / selR exchange the
+// halves of words fetched across the left / right end of the row
+template <int PARITY, bool SOLIDS>
+__device__ __forceinline__ void gather_pair(const WordPlanes& a, const WOff& o, uint32_t bits, uint32_t selL,
+                                            uint32_t selR, uint32_t (&w)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0 || (SOLIDS && ((bits >> OPP(i)) & 1u))) {
+            w[i] = __ldg(a.ptr(i, o.c));
+        } else {
+            const uint32_t v = __ldg(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
+            w[i] = EX(i) > 0 ? __byte_perm(v, 0u, selL) : (EX(i) < 0 ? __byte_perm(v, 0u, selR) : v);
+        }
+    }
+}
+
+// ... and the AA store of its post-collision words (the counterpart of store32)
+template <int PARITY, bool SOLIDS>
+__device__ __forceinline__ void store_pair(const WordPlanes& a, const WOff& o, uint32_t bits, uint32_t selL,
+                                           uint32_t selR, const uint32_t (&w)[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (PARITY == 0 || i == 0 || (SOLIDS && ((bits >> i) & 1u))) {
+            *a.ptr(OPP(i), o.c) = w[i];
+        } else {
+            const uint32_t v = EX(i) > 0 ? __byte_perm(w[i], 0u, selR) : (EX(i) < 0 ? __byte_perm(w[i], 0u, selL) : w[i]);
+            *a.ptr(i, o.nb(EX(i), EY(i), EZ(i))) = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void pair_offsets(WOff& o, int w, int y, int hx, int ny) {
+    o.wo[0] = (uint32_t)wrap1(w - 1, hx);
+    o.wo[1] = (uint32_t)w;
+    o.wo[2] = (uint32_t)wrap1(w + 1, hx);
+    o.yo[0] = (uint32_t)wrap1(y - 1, ny) * (uint32_t)hx;
+    o.yo[1] = (uint32_t)y * (uint32_t)hx;
+    o.yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)hx;
+}
+
+// collide-stream pass over pairs: tiles of 32 pairs x PR_BY rows (64 x PR_BY cells) marching
+// through a z-chunk, as collide_tile does for single cells.  The psi and writer-density rings
+// hold, per pair position, the value at the low cell's neighbour and the one at the high cell's
+// neighbour (exchanged where the position wraps around the row), in two planes, so that a warp
+// reading one cell's stencil reads consecutive words (no bank conflicts).
+constexpr int PR_BX = 32, PR_BY = 4, PR_NT = PR_BX * PR_BY;
+// Resident blocks per SM and the next-plane word prefetch, measured at 256^3 (collide ms, D3Q19 /
+// D3Q27): 4 / 3 blocks with prefetch 0.485 / 0.734 (no spills); 5 / 4 with prefetch 0.461 / 0.603
+// (a few spilled registers); 6 / 5 with prefetch 0.456 / 0.695; 6 / 5 without 0.452 / 0.651.
+// Kept: D3Q19 6 blocks without the prefetch, D3Q27 4 blocks with it.
+#ifndef LBM_PR_MINB19
+#define LBM_PR_MINB19 6
+#endif
+#ifndef LBM_PR_MINB27
+#define LBM_PR_MINB27 4
+#endif
+#ifndef LBM_PR_PREFETCH
+#define LBM_PR_PREFETCH (LBM_Q == 19 ? 0 : 1)
+#endif
+constexpr int PR_MINB = LBM_Q == 19 ? LBM_PR_MINB19 : LBM_PR_MINB27;
+constexpr int PR_RX = PR_BX + 2, PR_RY = PR_BY + 2, PR_RP = PR_RX * PR_RY;
+constexpr int PR_SLOTS = (PR_RP + PR_NT - 1) / PR_NT;
+
+// where this thread's ring entries come from: natural offset of the low cell within a plane,
+// whether the position lies in the domain, and whether its halves are exchanged
+struct PairRingSrc {
+    uint32_t off[PR_SLOTS];
+    bool ok[PR_SLOTS], sw[PR_SLOTS];
+};
+
+__device__ __forceinline__ void fetch_pair_plane(float2 (&v)[PR_SLOTS], const float* __restrict__ fld, int zz, int nz,
+                                                 int wall_z, uint32_t nxy, int hx, const PairRingSrc& g, int tid) {
+    bool zok = true;
+    if (zz < 0) { zok = !wall_z; zz += nz; } else if (zz >= nz) { zok = !wall_z; zz -= nz; }
+    const uint32_t zb = (uint32_t)zz * nxy;
+#pragma unroll
+    for (int s = 0; s < PR_SLOTS; ++s) {
+        const int k = tid + s * PR_NT;
+        if (k < PR_RP && zok && g.ok[s]) {
+            const float a = __ldg(fld + bounded(zb + g.off[s], (unsigned long long)nxy * nz));
+            const float b = __ldg(fld + bounded(zb + g.off[s] + hx, (unsigned long long)nxy * nz));
+            v[s] = g.sw[s] ? make_float2(b, a) : make_float2(a, b);
+        } else {
+            v[s] = make_float2(0.0f, 0.0f);
+        }
+    }
+}
+// a ring plane keeps the two halves apart (low cells' values, then high cells'), so that a warp
+// reading one cell's stencil touches consecutive words
+__device__ __forceinline__ void put_pair_plane(float (*slot)[PR_RP], const float2 (&v)[PR_SLOTS], int tid) {
+#pragma unroll
+    for (int s = 0; s < PR_SLOTS; ++s) {
+        const int k = tid + s * PR_NT;
+        if (k < PR_RP) {
+            slot[0][k] = v[s].x;
+            slot[1][k] = v[s].y;
+        }
+    }
+}
+
+// where a thread's ring entries come from (as collide_pair_kernel computes them)
+__device__ __forceinline__ PairRingSrc pair_ring_src(int w0, int y0, int hx, int nx, int ny, int wall_y, int tid) {
+    PairRingSrc src;
+#pragma unroll
+    for (int s = 0; s < PR_SLOTS; ++s) {
+        const int k = tid + s * PR_NT;
+        int pw = w0 - 1 + k % PR_RX, gy = y0 - 1 + k / PR_RX;
+        bool ok = k < PR_RP, sw = false;
+        if (pw < 0) { pw += hx; sw = true; } else if (pw >= hx) { pw -= hx; sw = true; }
+        if (gy < 0) { ok &= !wall_y; gy += ny; } else if (gy >= ny) { ok &= !wall_y; gy -= ny; }
+        // one wrap suffices for every position an active thread reads; anything still outside is unused
+        ok = ok && pw >= 0 && pw < hx && gy >= 0 && gy < ny;
+        src.ok[s] = ok;
+        src.sw[s] = sw;
+        src.off[s] = ok ? (uint32_t)gy * (uint32_t)nx + (uint32_t)pw : 0u;
+    }
+    return src;
+}
+
+// density + psi pass over pairs: the counterpart of psi_kernel for the paired layout, one plane per
+// block.  (A z-marching variant with the writers' densities in a shared ring, read at fixed offsets,
+// measured slower: 0.242 against 0.199 ms at 256^3 D3Q19; the per-population reads hit L1.)
+template <int PARITY, bool SOLIDS>
+__global__ void __launch_bounds__(PSI_BX * PSI_BY) psi_pair_kernel(KParams kp, float* __restrict__ psi,
+                                                                 unsigned* status, const float* __restrict__ rsrc,
+                                                                 float* __restrict__ rdst) {
+    const int hx = kp.hx, nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int w = blockIdx.x * PSI_BX + threadIdx.x, y = blockIdx.y * PSI_BY + threadIdx.y, z = blockIdx.z;
+    if (w >= hx || y >= ny) return;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    WOff o;
+    pair_offsets(o, w, y, hx, ny);
+    set_wplane(o, z, nz, (uint32_t)hx * (uint32_t)ny);
+    const uint32_t selL = w == 0 ? PERM_SWAP : PERM_KEEP, selR = w == hx - 1 ? PERM_SWAP : PERM_KEEP;
+    const uint32_t bits = SOLIDS ? solid_bits32<Q>(KGeom{kp}, nullptr, 0u, w, y, z) : 0u;
+    uint32_t wv[Q];
+    gather_pair<PARITY, SOLIDS>(WordPlanes{kp}, o, bits, selL, selR, wv);
+    // natural neighbourhoods of the two cells, for the writers' densities
+    Off32 on[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int x = w + h * hx;
+        on[h].xo[0] = (uint32_t)wrap1(x - 1, nx);
+        on[h].xo[1] = (uint32_t)x;
+        on[h].xo[2] = (uint32_t)wrap1(x + 1, nx);
+        on[h].yo[0] = (uint32_t)wrap1(y - 1, ny) * (uint32_t)nx;
+        on[h].yo[1] = (uint32_t)y * (uint32_t)nx;
+        on[h].yo[2] = (uint32_t)wrap1(y + 1, ny) * (uint32_t)nx;
+        set_plane(on[h], z, nz, nxy);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float p[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) p[i] = h ? half_hi(wv[i]) : half_lo(wv[i]);
+        denorm<Q, SOLIDS>(p, bits, RsOff32{rsrc, on[h]});
+        float rho = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += p[i];
+        rdst[on[h].c] = rho;
+        if (kp.multiphase) psi[bounded(on[h].c, (unsigned long long)nxy * nz)] = eval_psi(kp, rho, status);
+    }
+}
+
+template <int PARITY, bool SOLIDS, bool MULTIPHASE>
+__global__ void __launch_bounds__(PR_NT, PR_MINB) collide_pair_kernel(const KParams kp, const float* __restrict__ psi,
+                                                                     unsigned* status, int zchunk,
+                                                                     const float* __restrict__ rsrc,
+                                                                     const float* __restrict__ rown) {
+    __shared__ float ring[4][2][PR_RP];    // psi (low cells, high cells)
+    __shared__ float rring[4][2][PR_RP];   // densities the slots were written with
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + PR_BX * ty;
+    const int hx = kp.hx, nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const int w0 = blockIdx.x * PR_BX, y0 = blockIdx.y * PR_BY;
+    const int w = w0 + tx, y = y0 + ty;
+    const bool act = w < hx && y < ny;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny, wpl = (uint32_t)hx * (uint32_t)ny;
+    const int z0 = kp.zlo + (int)blockIdx.z * zchunk;
+    const int zend = min(z0 + zchunk, kp.zhi);
+    const KGeom g{kp};
+    const WordPlanes addr{kp};
+
+    const PairRingSrc src = pair_ring_src(w0, y0, hx, nx, ny, g.wall_y(), tid);
+    WOff o;
+    pair_offsets(o, w < hx ? w : 0, y < ny ? y : 0, hx, ny);
+    const uint32_t selL = w == 0 ? PERM_SWAP : PERM_KEEP, selR = w == hx - 1 ? PERM_SWAP : PERM_KEEP;
+    const uint32_t rowA = (uint32_t)(y < ny ? y : 0) * (uint32_t)nx + (uint32_t)(w < hx ? w : 0);   // low cell in its plane
+
+    // words and own densities of the first plane, then of plane z+1 while plane z is computed
+    uint32_t wn[Q];
+    float rn[2] = {0.0f, 0.0f};
+    uint32_t bits_n = 0u;
+    if (act) {
+        set_wplane(o, z0, nz, wpl);
+        bits_n = SOLIDS ? solid_bits32<Q>(g, nullptr, 0u, w, y, z0) : 0u;
+        gather_pair<PARITY, SOLIDS>(addr, o, bits_n, selL, selR, wn);
+        rn[0] = __ldg(rown + (uint32_t)z0 * nxy + rowA);
+        rn[1] = __ldg(rown + (uint32_t)z0 * nxy + rowA + hx);
+    }
+    float2 pv[PR_SLOTS], rv[PR_SLOTS];
+    if (MULTIPHASE) fetch_pair_plane(pv, psi, z0 + 1, nz, g.wall_z(), nxy, hx, src, tid);
+    fetch_pair_plane(rv, rsrc, z0 + 1, nz, g.wall_z(), nxy, hx, src, tid);
+    {
+        float2 t0[PR_SLOTS], t1[PR_SLOTS];
+        if (MULTIPHASE) {
+            fetch_pair_plane(t0, psi, z0 - 1, nz, g.wall_z(), nxy, hx, src, tid);
+            fetch_pair_plane(t1, psi, z0, nz, g.wall_z(), nxy, hx, src, tid);
+            put_pair_plane(ring[0], t0, tid);
+            put_pair_plane(ring[1], t1, tid);
+        }
+        fetch_pair_plane(t0, rsrc, z0 - 1, nz, g.wall_z(), nxy, hx, src, tid);
+        fetch_pair_plane(t1, rsrc, z0, nz, g.wall_z(), nxy, hx, src, tid);
+        put_pair_plane(rring[0], t0, tid);
+        put_pair_plane(rring[1], t1, tid);
+    }
+    const int lc = (ty + 1) * PR_RX + tx + 1;   // this pair's position in a ring plane
+    for (int z = z0, j = 0; z < zend; ++z, ++j) {
+        if (MULTIPHASE) {
+            put_pair_plane(ring[(j + 2) & 3], pv, tid);
+            if (z + 1 < zend) fetch_pair_plane(pv, psi, z + 2, nz, g.wall_z(), nxy, hx, src, tid);
+        }
+        put_pair_plane(rring[(j + 2) & 3], rv, tid);
+        if (z + 1 < zend) fetch_pair_plane(rv, rsrc, z + 2, nz, g.wall_z(), nxy, hx, src, tid);
+        __syncthreads();
+        if (!act) continue;
+        uint32_t wv[Q];
+        if (!LBM_PR_PREFETCH && z > z0) {   // no prefetch: this plane's words now
+            set_wplane(o, z, nz, wpl);
+            bits_n = SOLIDS ? solid_bits32<Q>(g, nullptr, 0u, w, y, z) : 0u;
+            gather_pair<PARITY, SOLIDS>(addr, o, bits_n, selL, selR, wn);
+            rn[0] = __ldg(rown + (uint32_t)z * nxy + rowA);
+            rn[1] = __ldg(rown + (uint32_t)z * nxy + rowA + hx);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) wv[i] = wn[i];
+        const float rown_c[2] = {rn[0], rn[1]};
+        const uint32_t bits = bits_n;
+        if (LBM_PR_PREFETCH && z + 1 < zend) {
+            set_wplane(o, z + 1, nz, wpl);
+            bits_n = SOLIDS ? solid_bits32<Q>(g, nullptr, 0u, w, y, z + 1) : 0u;
+            gather_pair<PARITY, SOLIDS>(addr, o, bits_n, selL, selR, wn);
+            rn[0] = __ldg(rown + (uint32_t)(z + 1) * nxy + rowA);
+            rn[1] = __ldg(rown + (uint32_t)(z + 1) * nxy + rowA + hx);
+        }
+        set_wplane(o, z, nz, wpl);
+        // wv ends up holding the outputs: the low cell's packed results replace the low halves it
+        // has consumed, then the high cell's replace the high halves (no second array of words)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float p[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) p[i] = h ? half_hi(wv[i]) : half_lo(wv[i]);
+            denorm<Q, SOLIDS>(p, bits, RsRing{&rring[j & 3][h][lc], &rring[(j + 1) & 3][h][lc],
+                                              &rring[(j + 2) & 3][h][lc], PR_RX});
+            Forces Fo;
+            if (MULTIPHASE) {
+                Fo = stencil_forces3<Q, SOLIDS>(kp, &ring[j & 3][h][lc], &ring[(j + 1) & 3][h][lc],
+                                                &ring[(j + 2) & 3][h][lc], PR_RX, bits);
+            } else {
+                Fo.fx = Fo.fy = Fo.fz = 0.f;
+                Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+                Fo.s2 = 0.f;
+            }
+            float rho, ux, uy, uz;
+            collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+            if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+            normalize<Q>(p, rown_c[h]);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t hv = (uint32_t)__half_as_ushort(__float2half_rn(p[i]));
+                wv[i] = h ? ((wv[i] & 0x0000ffffu) | (hv << 16)) : ((wv[i] & 0xffff0000u) | hv);
+            }
+        }
+        store_pair<PARITY, SOLIDS>(addr, o, bits, selL, selR, wv);
+    }
 }
 
 // ---- one-pass update with two population copies (periodic domains without solids, FP32).
@@ -326,15 +661,20 @@ __global__ void __launch_bounds__(32 * BY, MINB) collide_onepass_kernel(const KP
     Off32 o;
     pull_offsets(o, x % nx, y % ny, nx, ny);
     const int lc = (ty + 1) * RX + tx + 1;
-    // and, for the first HALO threads, one border cell of the ring plane
+    // and one border cell of the ring plane for HALO threads, spread evenly over the warps (the
+    // first lanes of each), so that every warp reaches the plane's barrier with the same work
+    constexpr int NWARP = BY, PER_WARP = (HALO + NWARP - 1) / NWARP;
+    static_assert(PER_WARP <= 32, "one border cell per lane at most");
+    const int hb = (tid & 31) < PER_WARP ? (tid >> 5) * PER_WARP + (tid & 31) : HALO;   // border index
+    const bool has_halo = hb < HALO;
     Off32 oh;
     int hl = 0;
-    if (MULTIPHASE && tid < HALO) {
+    if (MULTIPHASE && has_halo) {
         int rx, ry;
-        if (tid < RX) { rx = tid; ry = 0; }
-        else if (tid < 2 * RX) { rx = tid - RX; ry = RY - 1; }
-        else if (tid < 2 * RX + BY) { rx = 0; ry = 1 + tid - 2 * RX; }
-        else { rx = RX - 1; ry = 1 + tid - 2 * RX - BY; }
+        if (hb < RX) { rx = hb; ry = 0; }
+        else if (hb < 2 * RX) { rx = hb - RX; ry = RY - 1; }
+        else if (hb < 2 * RX + BY) { rx = 0; ry = 1 + hb - 2 * RX; }
+        else { rx = RX - 1; ry = 1 + hb - 2 * RX - BY; }
         hl = ry * RX + rx;
         pull_offsets(oh, (x0 - 1 + rx + nx) % nx, (y0 - 1 + ry + ny) % ny, nx, ny);
     }
@@ -349,7 +689,7 @@ __global__ void __launch_bounds__(32 * BY, MINB) collide_onepass_kernel(const KP
 #pragma unroll
             for (int i = 0; i < Q; ++i) rho += p[i];
             slot[lc] = eval_psi(kp, rho, status);
-            if (tid < HALO) {
+            if (has_halo) {
                 set_plane(oh, zz, nz, nxy);
                 float q[Q];
                 gather32<Q, 2, false>(rd, oh, 0u, q);
@@ -406,18 +746,18 @@ __global__ void pull_store_kernel(KParams kp, const float* __restrict__ fin, lon
 }
 
 // multi-domain collide-stream pass: one block per tile of any member of the launch's table;
-// physics by value
-template <int PARITY, bool SOLIDS, bool MULTIPHASE>
-__global__ void __launch_bounds__(ZM_NT, ZM_MINB) collide_batch_kernel(const KParams phys,
-                                                                      const __grid_constant__ BatchDomTable tab,
-                                                                      const BatchTile* __restrict__ tiles) {
-    __shared__ float ring[4][ZM_RP];
+// physics by value; tiles of shape S of BATCH_SHAPES
+template <int PARITY, bool SOLIDS, bool MULTIPHASE, int S>
+__global__ void __launch_bounds__(BatchTileShape<S>::NT, batch_minb<S>()) collide_batch_kernel(
+        const KParams phys, const __grid_constant__ BatchDomTable tab, const BatchTile* __restrict__ tiles) {
+    using TS = BatchTileShape<S>;
+    __shared__ float ring[4][TS::RP];
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const DomPlanes addr{m};
-    collide_tile<PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc,
-                                                           g.nz(), ring, nullptr, nullptr, nullptr);
+    collide_tile<TS, PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0,
+                                                                t.z0, t.zc, g.nz(), ring, nullptr, nullptr, nullptr);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -487,8 +827,13 @@ __global__ void init_kernel(KParams kp, void* __restrict__ fv, const float* __re
             }
         }
         if (F16) rdst[idx] = solid ? 1.0f : rho_in[idx];
+        long long pi = idx;
+        if (F16 && kp.paired) {
+            const int x = (int)(idx % kp.nx);
+            pi = idx - x + pair_pos(x, kp.hx);
+        }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) stpop(f + i * kp.plane + idx, out[i]);
+        for (int i = 0; i < Q; ++i) stpop(f + i * kp.plane + pi, out[i]);
     }
 }
 
@@ -522,7 +867,7 @@ __global__ void f16_pack_kernel(KParams kp, const float* __restrict__ fin, const
                 const float rw = own ? __ldg(rsrc + idx) : __ldg(rsrc + c.nb(-EX(i), -EY(i), -EZ(i)));
                 h = fin[i * n + idx] / rw - OMEGA<Q>(i);
             }
-            f[i * kp.plane + idx] = __float2half_rn(h);
+            f[i * kp.plane + c.pidx] = __float2half_rn(h);
         }
     }
 }
@@ -762,12 +1107,49 @@ void launch_gather_store(dim3 g, dim3 b, cudaStream_t st, const KParams& kp, int
     else gather_kernel<1, true, F16><<<g, b, 0, st>>>(kp, B.f, B.nbmask, out, B.rsrc);
 }
 
+// multi-domain launch helpers (internal linkage: each lattice's translation unit launches its own kernels)
+template <int S>
+cudaError_t launch_collide_batch_shape(const KParams& phys, const BatchDomTable& doms, const BatchTile* tiles,
+                                       int ntiles, int key, cudaStream_t st) {
+    const dim3 b(BATCH_SHAPES[S].bx, BATCH_SHAPES[S].by);
+    switch (key) {
+        case 0: collide_batch_kernel<0, false, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 1: collide_batch_kernel<0, false, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 2: collide_batch_kernel<0, true, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 3: collide_batch_kernel<0, true, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 4: collide_batch_kernel<1, false, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 5: collide_batch_kernel<1, false, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        case 6: collide_batch_kernel<1, true, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+        default: collide_batch_kernel<1, true, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_psi_batch_shape(const KParams& phys, const BatchDomTable& doms, const BatchTile* tiles, int ntiles,
+                                   int parity, int solids, cudaStream_t st) {
+    const dim3 b(BATCH_SHAPES[S].bx, BATCH_SHAPES[S].by);
+    if (parity == 0 && !solids) psi_batch_kernel<0, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else if (parity == 0) psi_batch_kernel<0, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else if (!solids) psi_batch_kernel<1, false, S><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    else psi_batch_kernel<1, true, S><<<ntiles, b, 0, st>>>(phys, doms, tiles);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define LBM_CAT2(a, b) a##b
 #define LBM_CAT(a, b) LBM_CAT2(a, b)
 
 cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B, cudaStream_t st) {
+    if (B.paired) {
+        const dim3 g((kp.hx + PSI_BX - 1) / PSI_BX, (kp.ny + PSI_BY - 1) / PSI_BY, kp.nz), b(PSI_BX, PSI_BY);
+        if (parity == 0 && !solids) psi_pair_kernel<0, false><<<g, b, 0, st>>>(kp, B.psi, B.status, B.rsrc, B.rnew);
+        else if (parity == 0) psi_pair_kernel<0, true><<<g, b, 0, st>>>(kp, B.psi, B.status, B.rsrc, B.rnew);
+        else if (!solids) psi_pair_kernel<1, false><<<g, b, 0, st>>>(kp, B.psi, B.status, B.rsrc, B.rnew);
+        else psi_pair_kernel<1, true><<<g, b, 0, st>>>(kp, B.psi, B.status, B.rsrc, B.rnew);
+        return cudaGetLastError();
+    }
     const dim3 g = psi_grid(kp), b(PSI_BX, PSI_BY);
     if (B.f16) launch_psi_store<true>(g, b, st, kp, parity, solids, B);
     else launch_psi_store<false>(g, b, st, kp, parity, solids, B);
@@ -781,7 +1163,7 @@ cudaError_t LBM_CAT(launch_psi_q, LBM_Q)(const KParams& kp, int parity, int soli
 // plane, the first loads with nothing to overlap them); and blocks differ in duration, which more
 // waves even out.  Over the chunk counts that give at least three waves, the choice minimises
 // (1 + h / zc) x ceil(waves) / waves x (1 + 0.2 / waves) (0.2 fitted to 256^3 sweeps).
-static int choose_zchunk(const KParams& kp, double h, int nz, int by = ZM_BY, int minb = ZM_MINB) {
+static int choose_zchunk(const KParams& kp, double h, int nz, int by, int minb) {
     if (kp.zchunk > 0) return kp.zchunk < nz ? kp.zchunk : nz;
     if (nz <= 1) return 1;
     static const int sms = [] {
@@ -814,10 +1196,32 @@ static int choose_zchunk(const KParams& kp, double h, int nz, int by = ZM_BY, in
 }
 
 // over the planes [zlo, zhi) the whole-grid collide kernels march through
-static int collide_zchunk(const KParams& kp) { return choose_zchunk(kp, 1.0, kp.zhi - kp.zlo); }
+static int collide_zchunk(const KParams& kp) { return choose_zchunk(kp, 1.0, kp.zhi - kp.zlo, ZM_BY, ZM_MINB); }
 
 cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int solids, const Bufs& B,
                                              cudaStream_t st) {
+    if (B.paired) {
+        // tiles of 32 pairs: the z-chunk choice counts columns of hx words
+        KParams kw = kp;
+        kw.nx = kp.hx;
+        const int planes = kp.zhi - kp.zlo;
+        const int zc = choose_zchunk(kw, 1.0, planes, PR_BY, PR_MINB);
+        const dim3 g((kp.hx + PR_BX - 1) / PR_BX, (kp.ny + PR_BY - 1) / PR_BY, (planes + zc - 1) / zc), b(PR_BX, PR_BY);
+        const int key = parity * 4 + (solids ? 2 : 0) + (kp.multiphase ? 1 : 0);
+        const float* r0 = B.rsrc;
+        const float* r1 = B.rnew;
+        switch (key) {
+            case 0: collide_pair_kernel<0, false, false><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 1: collide_pair_kernel<0, false, true><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 2: collide_pair_kernel<0, true, false><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 3: collide_pair_kernel<0, true, true><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 4: collide_pair_kernel<1, false, false><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 5: collide_pair_kernel<1, false, true><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            case 6: collide_pair_kernel<1, true, false><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+            default: collide_pair_kernel<1, true, true><<<g, b, 0, st>>>(kp, B.psi, B.status, zc, r0, r1); break;
+        }
+        return cudaGetLastError();
+    }
     const int zc = collide_zchunk(kp);
     const int planes = kp.zhi - kp.zlo;
     const dim3 g((kp.nx + ZM_BX - 1) / ZM_BX, (kp.ny + ZM_BY - 1) / ZM_BY, (planes + zc - 1) / zc), b(ZM_BX, ZM_BY);
@@ -828,33 +1232,31 @@ cudaError_t LBM_CAT(launch_collide_q, LBM_Q)(const KParams& kp, int parity, int 
 
 cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,
                                                    const BatchTile* tiles, int ntiles, int parity, int solids,
-                                                   cudaStream_t st) {
+                                                   int shape, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    const dim3 b(ZM_BX, ZM_BY);
     const int key = parity * 4 + (solids ? 2 : 0) + (phys.multiphase ? 1 : 0);
-    switch (key) {
-        case 0: collide_batch_kernel<0, false, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 1: collide_batch_kernel<0, false, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 2: collide_batch_kernel<0, true, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 3: collide_batch_kernel<0, true, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 4: collide_batch_kernel<1, false, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 5: collide_batch_kernel<1, false, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        case 6: collide_batch_kernel<1, true, false><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
-        default: collide_batch_kernel<1, true, true><<<ntiles, b, 0, st>>>(phys, doms, tiles); break;
+    switch (shape) {
+        case 0: return launch_collide_batch_shape<0>(phys, doms, tiles, ntiles, key, st);
+        case 1: return launch_collide_batch_shape<1>(phys, doms, tiles, ntiles, key, st);
+        case 2: return launch_collide_batch_shape<2>(phys, doms, tiles, ntiles, key, st);
+        case 3: return launch_collide_batch_shape<3>(phys, doms, tiles, ntiles, key, st);
+        case 4: return launch_collide_batch_shape<4>(phys, doms, tiles, ntiles, key, st);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,
-                                               const BatchTile* tiles, int ntiles, int parity, int solids,
+                                               const BatchTile* tiles, int ntiles, int parity, int solids, int shape,
                                                cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    const dim3 b(PSI_BX, PSI_BY);
-    if (parity == 0 && !solids) psi_batch_kernel<0, false><<<ntiles, b, 0, st>>>(phys, doms, tiles);
-    else if (parity == 0) psi_batch_kernel<0, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
-    else if (!solids) psi_batch_kernel<1, false><<<ntiles, b, 0, st>>>(phys, doms, tiles);
-    else psi_batch_kernel<1, true><<<ntiles, b, 0, st>>>(phys, doms, tiles);
-    return cudaGetLastError();
+    switch (shape) {
+        case 0: return launch_psi_batch_shape<0>(phys, doms, tiles, ntiles, parity, solids, st);
+        case 1: return launch_psi_batch_shape<1>(phys, doms, tiles, ntiles, parity, solids, st);
+        case 2: return launch_psi_batch_shape<2>(phys, doms, tiles, ntiles, parity, solids, st);
+        case 3: return launch_psi_batch_shape<3>(phys, doms, tiles, ntiles, parity, solids, st);
+        case 4: return launch_psi_batch_shape<4>(phys, doms, tiles, ntiles, parity, solids, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, const Bufs& B, float thr, int* out,
@@ -901,8 +1303,6 @@ cudaError_t LBM_CAT(launch_pull_store_q, LBM_Q)(const KParams& kp, const float* 
     return cudaGetLastError();
 }
 
-int LBM_CAT(tile_height_q, LBM_Q)() { return ZM_BY; }
-int LBM_CAT(resident_blocks_q, LBM_Q)() { return ZM_MINB; }
 
 cudaError_t LBM_CAT(launch_init_q, LBM_Q)(const KParams& kp, const Bufs& B, const float* rho, const float* u,
                                           cudaStream_t st) {

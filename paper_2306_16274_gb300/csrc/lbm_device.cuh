@@ -114,18 +114,28 @@ template <int Q>
 __host__ __device__ constexpr int MP(int k) { return (Q == 27 || k < 16) ? k : k - 1; }
 
 // ------------------------------------------------------------------ neighbourhood of a cell
+// idx / nb(): cell indices of the natural layout (fields, and populations unless paired);
+// pidx / pnb(): population slot indices, which differ only in the x-paired FP16 layout.
 struct Cell {
     int x, y, z;
-    long long idx;
+    long long idx, pidx;
     int xo[3];        // x-1, x, x+1 wrapped (periodic)
+    int pxo[3];       // their slot positions within a row (= xo unless paired)
     long long yo[3];  // (y+dy)*nx wrapped
     long long zo[3];  // (z+dz)*nx*ny wrapped
     __device__ __forceinline__ long long nb(int dx, int dy, int dz) const {
         return zo[dz + 1] + yo[dy + 1] + xo[dx + 1];
     }
+    __device__ __forceinline__ long long pnb(int dx, int dy, int dz) const {
+        return zo[dz + 1] + yo[dy + 1] + pxo[dx + 1];
+    }
 };
 
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// slot position of cell x within its row in the x-paired layout: word x mod hx, low half for
+// x < hx, high half otherwise
+__host__ __device__ __forceinline__ int pair_pos(int x, int hx) { return x < hx ? 2 * x : 2 * (x - hx) + 1; }
 
 __device__ __forceinline__ Cell make_cell(const KParams& kp, int x, int y, int z) {
     Cell c;
@@ -133,13 +143,15 @@ __device__ __forceinline__ Cell make_cell(const KParams& kp, int x, int y, int z
     c.y = y;
     c.z = z;
     const long long nxy = (long long)kp.nx * kp.ny;
-    c.idx = z * nxy + (long long)y * kp.nx + x;
 #pragma unroll
     for (int d = -1; d <= 1; ++d) {
         c.xo[d + 1] = wrap1(x + d, kp.nx);
+        c.pxo[d + 1] = kp.paired ? pair_pos(c.xo[d + 1], kp.hx) : c.xo[d + 1];
         c.yo[d + 1] = (long long)wrap1(y + d, kp.ny) * kp.nx;
         c.zo[d + 1] = (long long)wrap1(z + d, kp.nz) * nxy;
     }
+    c.idx = z * nxy + (long long)y * kp.nx + x;
+    c.pidx = z * nxy + (long long)y * kp.nx + c.pxo[1];
     return c;
 }
 
@@ -169,13 +181,13 @@ __device__ __forceinline__ void gather(const KParams& kp, const T* __restrict__ 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 2) {   // one-pass layout: pull from x - e_i
-            p[i] = ldpop(f + i * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
+            p[i] = ldpop(f + i * kp.plane + c.pnb(-EX(i), -EY(i), -EZ(i)));
         } else if (PARITY == 0 || i == 0) {
-            p[i] = ldpop(f + i * kp.plane + c.idx);
+            p[i] = ldpop(f + i * kp.plane + c.pidx);
         } else if (SOLIDS && ((bits >> OPP(i)) & 1u)) {
-            p[i] = ldpop(f + i * kp.plane + c.idx);   // reflected at the wall in the previous step
+            p[i] = ldpop(f + i * kp.plane + c.pidx);   // reflected at the wall in the previous step
         } else {
-            p[i] = ldpop(f + OPP(i) * kp.plane + c.nb(-EX(i), -EY(i), -EZ(i)));
+            p[i] = ldpop(f + OPP(i) * kp.plane + c.pnb(-EX(i), -EY(i), -EZ(i)));
         }
     }
 }
@@ -203,13 +215,15 @@ __device__ __forceinline__ void normalize(float (&p)[Q], float rho) {
 
 // density field lookups for denorm: three ring planes in shared memory, a 32-bit neighbourhood,
 // or a 64-bit one
-struct RsRing {
+template <int SX = 1>
+struct RsRingT {
     const float *pm, *p0, *pp;
     int sy;
     __device__ __forceinline__ float at(int dx, int dy, int dz) const {
-        return (dz < 0 ? pm : (dz > 0 ? pp : p0))[dx + dy * sy];
+        return (dz < 0 ? pm : (dz > 0 ? pp : p0))[SX * dx + dy * sy];
     }
 };
+using RsRing = RsRingT<1>;
 struct RsCell {
     const float* r;
     const Cell& c;
@@ -551,8 +565,8 @@ __device__ __forceinline__ void store32(const A& a, const Off32& o, uint32_t bit
 }
 
 // Forces from three psi planes (z-1, z, z+1); each pointer addresses psi(x) within its plane,
-// x stride 1 and y stride sy.
-template <int Q, bool SOLIDS>
+// x stride SX and y stride sy.
+template <int Q, bool SOLIDS, int SX = 1>
 __device__ __forceinline__ Forces stencil_forces3(const KParams& kp, const float* pm, const float* p0, const float* pp,
                                                   int sy, uint32_t bits) {
     const float pc = p0[0];
@@ -562,7 +576,7 @@ __device__ __forceinline__ Forces stencil_forces3(const KParams& kp, const float
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const float* pl = EZ(i) < 0 ? pm : (EZ(i) > 0 ? pp : p0);
-        pn[i] = pl[EX(i) + EY(i) * sy];
+        pn[i] = pl[SX * EX(i) + EY(i) * sy];
         if (SOLIDS && ((bits >> i) & 1u)) {   // a solid neighbour: psi(x) there, and F_ads
             pn[i] = pc;
             Ax += WN<Q>(i) * EX(i);

@@ -43,6 +43,11 @@ struct KParams {
     int zchunk;                   // z planes per collide block (0 = automatic)
     int zlo, zhi;                 // planes [zlo, zhi) the whole-grid collide kernels march through
     float* gq[27];                // one-pass layout: planes of the copy the step writes
+    // shifted FP16 store in the x-paired layout (even nx, x periodic, no solid mask): word w of a
+    // row holds cells w (low half) and w + hx (high half), hx = nx / 2, so a shift by one cell in
+    // x moves both cells of a word to one other word
+    int paired;
+    int hx;
 };
 
 // Geometry and device buffers of one member of a multi-domain launch (its physics come from the
@@ -63,11 +68,22 @@ struct BatchDomTable {
     BatchDom d[BATCH_LAUNCH_DOMS];
 };
 
-// One block of a multi-domain launch: member d of the launch's table, cells [x0, x0+32) x [y0, y0+tile height)
-// x [z0, z0+zc) (clipped to the domain).
+// One block of a multi-domain launch: member d of the launch's table, cells [x0, x0+tile width) x
+// [y0, y0+tile height) x [z0, z0+zc) (clipped to the domain).
 struct BatchTile {
     int d, x0, y0, z0, zc;
 };
+
+// Tile shapes of the multi-domain kernels, compiled for each lattice; lbm_batch_tune picks one per
+// group.  Width and height of a tile in cells (one thread each) and the resident blocks per SM the
+// collide kernel is compiled for on D3Q19 / D3Q27 (its register budget).  Narrower tiles waste fewer
+// lanes on domains whose x extent is not a multiple of 32; lower residency leaves more registers.
+struct BatchShape {
+    int bx, by, minb19, minb27;
+};
+constexpr int BATCH_NSHAPES = 5;
+constexpr BatchShape BATCH_SHAPES[BATCH_NSHAPES] = {
+    {32, 4, 7, 5}, {32, 2, 14, 10}, {16, 8, 7, 5}, {16, 4, 14, 10}, {32, 4, 6, 4}};
 
 // Device buffers of one context's launches.  f: the population slots, floats or (f16) the
 // shifted FP16 store; rsrc: the densities the stored slots were written with; rnew: the other
@@ -78,6 +94,7 @@ struct Bufs {
     const uint32_t* nbmask;
     unsigned* status;
     int f16;
+    int paired;                   // f16 in the x-paired layout (KParams::paired)
     const float* rsrc;
     float* rnew;
 };
@@ -100,17 +117,15 @@ struct Bufs {
                                    float* out, cudaStream_t st);                                     \
     cudaError_t launch_collide_batch_q##Q(const KParams& phys, const BatchDomTable& tab,             \
                                           const BatchTile* tiles, int ntiles, int parity, int solids,  \
-                                          cudaStream_t st);                                           \
+                                          int shape, cudaStream_t st);                                \
     cudaError_t launch_psi_batch_q##Q(const KParams& phys, const BatchDomTable& tab,                 \
                                       const BatchTile* tiles, int ntiles, int parity, int solids,      \
-                                      cudaStream_t st);                                               \
+                                      int shape, cudaStream_t st);                                    \
     cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const Bufs& B, float thr, int* out, \
                                     cudaStream_t st);                                               \
     cudaError_t launch_onepass_q##Q(const KParams& kp, unsigned* status, cudaStream_t st);          \
     cudaError_t launch_pull_store_q##Q(const KParams& kp, const float* fin, long long fstride,       \
                                        float* fout, cudaStream_t st);                               \
-    int tile_height_q##Q();                                                                         \
-    int resident_blocks_q##Q();                                                                     \
     unsigned long long bounds_violations_q##Q();
 
 LBM_DECLARE_LAUNCHERS(19)

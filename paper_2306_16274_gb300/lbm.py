@@ -18,6 +18,7 @@ LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(_HERE, "liblbm.so")
 
 EOS = {"none": 0, "cs": 1, "piecewise": 2}
 STORE = {"fp32": 0, "fp16": 1}
+LAYOUT = {"auto": 0, "single": 1}
 BC = {"periodic": 0, "wall": 1}
 RATE_NAMES = ("s0", "s1", "s2", "s2b", "s3", "s3b", "s4", "s4b", "s5", "s6")
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_UNSTABLE",
@@ -38,7 +39,7 @@ class lbm_params(ctypes.Structure):
         ("s", ctypes.c_double * 10), ("variable_nu", ctypes.c_int32),
         ("nu_l", ctypes.c_double), ("nu_v", ctypes.c_double), ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
         ("g", ctypes.c_double * 3), ("psi_ext_rho", ctypes.c_double), ("zchunk", ctypes.c_int32),
-        ("store", ctypes.c_int32), ("onepass", ctypes.c_int32),
+        ("store", ctypes.c_int32), ("onepass", ctypes.c_int32), ("store_layout", ctypes.c_int32),
     ]
 
 
@@ -81,6 +82,9 @@ def lib():
         "lbm_batch_sync": (I32, [P]),
         "lbm_batch_tune": (I32, [P, I32, ctypes.POINTER(I32), I32]),
         "lbm_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "lbm_batch_group": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                  ctypes.POINTER(I32)]),
+        "lbm_batch_set_group": (I32, [P, I32, I32, I32]),
         "lbm_batch_destroy": (V, [P]),
         "lbm_batch_last_error": (ctypes.c_char_p, [P]),
         "lbm_debug_bounds_violations": (ctypes.c_uint64, []),
@@ -99,7 +103,8 @@ class Params:
     eos "none" / "cs" (eos_p = a, b, R, T) / "piecewise" (rho1, rho2, theta_v, theta_m, theta_l);
     rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library);
     store "fp32" or "fp16" (shifted FP16 population store); onepass: one pass per step over two
-    population copies (periodic, no solids, FP32)."""
+    population copies (periodic, no solids, FP32); store_layout "auto" (FP16 slots of cells x and
+    x + nx/2 share a word where nx is even, x periodic and no mask is given) or "single"."""
     lattice: int = 19
     shape: tuple = (32, 32, 32)
     bc: tuple = ("periodic", "periodic", "periodic")
@@ -120,6 +125,7 @@ class Params:
     zchunk: int = 0
     store: str = "fp32"
     onepass: bool = False
+    store_layout: str = "auto"
 
     def to_c(self):
         c = lbm_params()
@@ -144,6 +150,7 @@ class Params:
         c.zchunk = int(self.zchunk)
         c.store = STORE[self.store] if isinstance(self.store, str) else int(self.store)
         c.onepass = 1 if self.onepass else 0
+        c.store_layout = LAYOUT[self.store_layout] if isinstance(self.store_layout, str) else int(self.store_layout)
         return c
 
     @property
@@ -406,12 +413,26 @@ class Batch:
         self._check(self._L.lbm_batch_sync(self._b))
 
     def tune(self, trial_steps=3):
-        """Pick the z-chunk per group by timing; returns the choices (0 = automatic)."""
+        """Pick the tile shape and then the z-chunk per group by timing; returns the z-chunks
+        (0 = automatic); groups() gives the shapes."""
         g = ctypes.c_int32()
         self._check(self._L.lbm_batch_info(self._b, ctypes.byref(g), None, None))
         out = (ctypes.c_int32 * max(g.value, 1))()
         self._check(self._L.lbm_batch_tune(self._b, int(trial_steps), out, g.value))
         return list(out)[:g.value]
+
+    def groups(self):
+        """[{lattice, solids, shape, zchunk}] per group (shape: index of LBM_BATCH_SHAPES)."""
+        n = self.info()["groups"]
+        out = []
+        for k in range(n):
+            v = [ctypes.c_int32() for _ in range(4)]
+            self._check(self._L.lbm_batch_group(self._b, k, *[ctypes.byref(x) for x in v]))
+            out.append(dict(zip(("lattice", "solids", "shape", "zchunk"), [x.value for x in v])))
+        return out
+
+    def set_group(self, group, shape, zchunk=0):
+        self._check(self._L.lbm_batch_set_group(self._b, int(group), int(shape), int(zchunk)))
 
     def info(self):
         g, t, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -2,12 +2,20 @@
 
 Requests (``JobSpec``) arrive over time.  The server admits them first come, first served,
 while the device memory they need -- computed beforehand by ``lbm_estimate_bytes`` -- fits a
-budget and a slot is free; keeps their populations resident; advances every admitted job
-together in ticks of a fixed, even number of steps (one multi-domain ``Batch`` launch
-sequence per tick, rebuilt when the set of jobs changes); reads each job's contact detector
-after every tick with one device-to-host copy; and retires a job when it has run its step cap
-or, for impact jobs, when its droplet has left the solid (contact time, Sec. III E / IV B),
-freeing its memory for the next request.
+budget and a slot is free; keeps their populations resident; advances admitted jobs together in
+ticks of a fixed, even number of steps (one multi-domain ``Batch`` launch sequence per tick,
+rebuilt when the set of jobs changes); reads each advanced job's contact detector after the tick
+with one device-to-host copy; and retires a job when it has run its step cap or, for impact
+jobs, when its droplet has left the solid (contact time, Sec. III E / IV B), freeing its memory
+for the next request.
+
+Which resident jobs a tick advances is the scheduling policy.  "all": every resident job (the
+GPU is shared evenly; best aggregate throughput when many jobs are resident).  "aged_srpt": the
+``max_batch`` jobs with the smallest priority value, remaining work (cells x remaining steps
+over the measured cell-update rate, in seconds) minus ``alpha`` times the time the job has
+waited since it arrived -- short jobs finish first (low median time-to-result) and a long job's
+priority rises as it waits, so it is not starved (bounded tail); the few jobs advanced together
+still share one batch launch.
 
 A job's trajectory and every observation depend only on its own inputs and on the tick length:
 observations fall on job-local steps that are multiples of the tick, the batch kernels are
@@ -83,16 +91,37 @@ class Server:
     """Admission, ticking and retirement over an engine (see module docstring).
 
     budget_bytes: device memory the resident jobs may hold; max_active: slot count;
-    tick: steps per tick (even: every job stays at the even AA phase between ticks)."""
+    tick: steps per tick (even: every job stays at the even AA phase between ticks);
+    policy: "all" or "aged_srpt" (with alpha, max_batch); rate: initial estimate of the
+    cell updates per second, refined from every tick."""
 
-    def __init__(self, engine, budget_bytes, tick=100, max_active=64, clock=time.perf_counter, sleep=time.sleep):
+    POLICIES = ("all", "aged_srpt")
+
+    def __init__(self, engine, budget_bytes, tick=100, max_active=64, clock=time.perf_counter, sleep=time.sleep,
+                 policy="all", alpha=1.0, max_batch=2, rate=1.6e10):
         if tick < 2 or tick % 2:
             raise ValueError("tick must be an even number of steps >= 2")
         if max_active < 1:
             raise ValueError("max_active must be >= 1")
+        if policy not in self.POLICIES:
+            raise ValueError(f"policy must be one of {self.POLICIES}")
+        if max_batch < 1 or alpha < 0 or not rate > 0:
+            raise ValueError("max_batch must be >= 1, alpha >= 0 and rate > 0")
         self.engine, self.budget, self.tick, self.max_active = engine, int(budget_bytes), int(tick), int(max_active)
         self.clock, self.sleep = clock, sleep
+        self.policy, self.alpha, self.max_batch, self.rate = policy, float(alpha), int(max_batch), float(rate)
         self.stats = {}
+
+    def select(self, active, now):
+        """The resident jobs the next tick advances (see the module docstring)."""
+        if self.policy == "all":
+            return list(active)
+
+        def priority(s):
+            remaining = max(s.spec.steps - s.step, 0) * s.result.cells / self.rate
+            return (remaining - self.alpha * (now - s.spec.arrival), s.spec.arrival)
+
+        return sorted(active, key=priority)[:self.max_batch]
 
     def run(self, specs):
         """Serve `specs` (arrival times in seconds from the start of the run); returns JobResults in
@@ -139,13 +168,18 @@ class Server:
                         self.sleep(min(wait, 0.05))
                 continue
             tb = self.clock()
-            handles = [s.handle for s in active]
+            run = self.select(active, tb - t0)
+            handles = [s.handle for s in run]
             self.engine.advance(handles, self.tick)
-            obs = self.engine.observe(handles, [s.spec.threshold for s in active])
+            obs = self.engine.observe(handles, [s.spec.threshold for s in run])
             status = self.engine.status(handles)
-            busy += self.clock() - tb
+            dt = self.clock() - tb
+            busy += dt
             ticks += 1
-            for s, o, st in zip(active, obs, status):
+            work = sum(s.result.cells for s in run) * self.tick
+            if dt > 0:
+                self.rate = 0.8 * self.rate + 0.2 * work / dt
+            for s, o, st in zip(run, obs, status):
                 s.step += self.tick
                 cell_steps += s.result.cells * self.tick
                 r = s.result
@@ -192,19 +226,21 @@ class Server:
 class GpuEngine:
     """Runs jobs through liblbm.so on the current CUDA device, all on one stream.
 
-    batched=True advances the resident jobs with one multi-domain Batch (rebuilt when the set
-    changes; a lone job steps alone); batched=False steps each job with its own single-domain
-    launches.  keep_populations:
-    copy every finished job's populations to the host (for equality checks)."""
+    batched=True advances the jobs of a tick with one multi-domain Batch (a lone job steps
+    alone); the last `cache` batches are kept, keyed by their member set, so a scheduler that
+    alternates between a few sets does not rebuild them every tick.  batched=False steps each
+    job with its own single-domain launches.  keep_populations: copy every finished job's
+    populations to the host (for equality checks)."""
 
-    def __init__(self, batched=True, stream=None, keep_populations=False):
+    def __init__(self, batched=True, stream=None, keep_populations=False, cache=8):
         import torch
+        from collections import OrderedDict
         self.torch = torch
         self.batched = batched
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.keep_populations = keep_populations
-        self._batch = None
-        self._batch_key = None
+        self._batches = OrderedDict()
+        self._cache = max(1, int(cache))
         self._obs = None
         self.launch_sets = 0
 
@@ -230,30 +266,29 @@ class GpuEngine:
         return sim
 
     def release(self, sim):
-        if self._batch is not None and sim in self._batch.sims:
-            self._batch.close()
-            self._batch, self._batch_key = None, None
+        for key in [k for k, b in self._batches.items() if sim in b.sims]:
+            self._batches.pop(key).close()
         sim.close()
 
     def advance(self, sims, n):
         if not self.batched or len(sims) == 1:
-            # a lone resident job takes its own single-domain launches (the whole-grid kernels
-            # where its geometry allows), faster than a one-member batch; results are the same
-            if self._batch is not None:
-                self._batch.close()
-                self._batch, self._batch_key = None, None
+            # a lone job takes its own single-domain launches (the whole-grid kernels where its
+            # geometry allows), faster than a one-member batch; results are the same
             for s in sims:
                 s.step(n)
             self.launch_sets += len(sims)
             return
-        key = tuple(id(s) for s in sims)
-        if key != self._batch_key:
-            if self._batch is not None:
-                self._batch.close()
-            self._batch = Batch(sims, stream=self.stream)
-            self._batch_key = key
+        key = tuple(sorted(id(s) for s in sims))
+        b = self._batches.get(key)
+        if b is None:
+            while len(self._batches) >= self._cache:
+                self._batches.popitem(last=False)[1].close()
+            b = Batch(sims, stream=self.stream)
+            self._batches[key] = b
             self.launch_sets += 1
-        self._batch.step(n)
+        else:
+            self._batches.move_to_end(key)
+        b.step(n)
 
     def observe(self, sims, thresholds):
         torch = self.torch
@@ -290,9 +325,8 @@ class GpuEngine:
         return tuple(float(v) for v in sums), pops
 
     def close(self):
-        if self._batch is not None:
-            self._batch.close()
-            self._batch = None
+        while self._batches:
+            self._batches.popitem()[1].close()
 
 
 def percentile(values, q):

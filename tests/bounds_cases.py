@@ -31,6 +31,11 @@ def main():
         out[f"periodic{Q}"] = digest(U.run_gpu(d, rho, u, steps=7))
         out[f"onepass{Q}"] = digest(U.run_gpu(dict(d, onepass=True), rho, u, steps=7))
         out[f"fp16_{Q}"] = digest(U.run_gpu(dict(d, store="fp16"), rho, u, steps=7))
+        # even nx: the x-paired FP16 layout and its pair kernels, periodic and with y / z walls
+        sp = (34, 30, 28)
+        rp, up = W.droplet(sp, 8.0, rl, rv, W=3.0)
+        out[f"fp16p_{Q}"] = digest(U.run_gpu(dict(d, shape=sp, store="fp16"), rp, up, steps=7))
+        out[f"fp16pw_{Q}"] = digest(U.run_gpu(dict(d, shape=sp, store="fp16", bc=(0, 1, 1)), rp, up, steps=7))
         shape = (40, 36, 24)
         rho, u = W.impact(shape, 7.0, rlp, rvp, U=0.05, gap=2.0)
         dw = dict(lattice=Q, shape=shape, bc=(0, 0, 1), sigma=0.1, G_ads=0.1, **kwp)

@@ -90,6 +90,23 @@ def test_per_lattice_launch_helpers_have_internal_linkage(lib):
     for r in rows:
         kind = r.split()[1] if len(r.split()) > 2 else r.split()[0]
         assert kind in ("t", "d", "b", "r"), r
+    # and more generally: every external symbol of the kernels' namespace is either a per-lattice
+    # entry point (suffix _q19 / _q27) or lattice independent; a template helper instantiated in
+    # both lattice units would be folded by the linker
+    import re
+    shared = {"launch_nbmask", "launch_finish_sums", "launch_contact_init", "set_thread_error",
+              "moments_partial_blocks"}
+    checked = 0
+    for r in out.splitlines():
+        parts = r.split(None, 2)
+        if len(parts) < 3 or parts[1] not in ("T", "W", "V", "D", "B", "R", "u"):
+            continue
+        m = re.search(r"(?:^|[\s*&])lbm::(\w+)", parts[2].split("(")[0])
+        if not m:
+            continue
+        checked += 1
+        assert re.search(r"_q(19|27)$", m.group(1)) or m.group(1) in shared, r
+    assert checked > 0
 
 
 def test_extent_limit_is_enforced(lib):

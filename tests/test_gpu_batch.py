@@ -83,7 +83,7 @@ def test_batch_replay_and_tuning_keep_results():
     b.step(8)
     b.sync()
     total = together[0].step_count
-    assert total == 6 + 5 + 7 * 3 + 8
+    assert total == 6 + 5 + 12 * 3 + 8     # the tuner advances 12 x (trial_steps + 1) steps
     for a in alone:
         a.step(total)
     for a, t in zip(alone, together):
@@ -191,3 +191,73 @@ def test_zwall_domain_split_equals_batch(Q, shape, zchunk):
         a.step(n)
         bb.step(n)
         assert np.array_equal(a.populations(device=False), b.populations(device=False)), (n,)
+
+
+def test_every_tile_shape_equals_members_stepped_alone():
+    # each compiled tile shape of the multi-domain kernels (32 x 4, 32 x 2, 16 x 8, 16 x 4, and 32 x 4
+    # at fewer resident blocks) forced on every group, with automatic and fixed z-chunks: the members
+    # still evolve bitwise as when stepped alone, after odd and even step counts
+    from paper_2306_16274_gb300 import Batch
+    from paper_2306_16274_gb300.lbm import lib
+    nshapes = 5
+    m = _members()
+    alone = _make(m)
+    for s in alone:
+        s.step(3 * nshapes)
+    together = _make(m)
+    b = Batch(together)
+    for shape in range(nshapes):
+        for g in range(b.info()["groups"]):
+            b.set_group(g, shape, 0 if shape % 2 == 0 else 3)
+        assert all(gr["shape"] == shape for gr in b.groups())
+        b.step(3)
+    b.sync()
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
+    # unknown shapes and groups are refused
+    with pytest.raises(Exception):
+        b.set_group(0, nshapes, 0)
+    with pytest.raises(Exception):
+        b.set_group(b.info()["groups"], 0, 0)
+    assert lib().lbm_batch_group(b._b, -1, None, None, None, None) == 1
+    b.close()
+
+
+def test_tuner_picks_a_shape_per_group_and_keeps_results():
+    from paper_2306_16274_gb300 import Batch
+    m = _members()
+    alone = _make(m)
+    together = _make(m)
+    b = Batch(together)
+    zc = b.tune(trial_steps=1)
+    groups = b.groups()
+    assert len(zc) == len(groups) == b.info()["groups"]
+    assert all(0 <= g["shape"] < 5 and g["zchunk"] == z for g, z in zip(groups, zc))
+    tuned_steps = together[0].step_count
+    for s in alone:
+        s.step(tuned_steps + 4)
+    b.step(4)
+    b.sync()
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
+    b.close()
+
+
+def test_mixed_shapes_across_groups_keep_partners_aligned():
+    # different shapes on different groups: a member's solid-free and solid groups are cut into the
+    # same columns (setting one sets the other), so its cells are still covered exactly once
+    from paper_2306_16274_gb300 import Batch
+    m = _members()
+    alone = _make(m)
+    together = _make(m)
+    b = Batch(together)
+    n = b.info()["groups"]
+    for g in range(n):
+        b.set_group(g, (g * 2 + 1) % 5, g % 3)
+    b.step(9)
+    b.sync()
+    for s in alone:
+        s.step(9)
+    for a, t in zip(alone, together):
+        assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy())
+    b.close()

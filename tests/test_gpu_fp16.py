@@ -111,3 +111,50 @@ def test_fp16_contexts_cannot_join_a_batch():
     with pytest.raises(LBMError) as e:
         Batch([sim])
     assert e.value.status == 1
+
+
+def _paired_cases():
+    kw, rl, rv = U.cs_eos("T0.7")
+    kwp, rlp, rvp = U.pw_eos()
+    out = []
+    for Q in (19, 27):
+        # hx = 17: one ragged tile of pairs; hx = 35: a full and a ragged tile; z-chunks of 3 planes
+        for shape in ((34, 11, 9), (70, 6, 7)):
+            rho, u = W.droplet(shape, 3.0, rl, rv, W=3.0)
+            out.append((f"drop{Q}_{shape[0]}", dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.3, zchunk=3,
+                                                    g=(1e-5, 0.0, 0.0), **kw), rho, u))
+        shape = (40, 12, 10)
+        rho, u = W.impact(shape, 4.0, rlp, rvp, U=0.05, gap=2.0)
+        out.append((f"zwall{Q}", dict(lattice=Q, shape=shape, bc=(0, 1, 1), sigma=0.1, G_ads=0.1, zchunk=3, **kwp),
+                    rho, u))
+        # nx = 2: one word per row, both halves exchanged by every x shift
+        r = 0.2 + 0.02 * np.random.default_rng(3).random((3, 5, 2))
+        out.append((f"nx2_{Q}", dict(lattice=Q, shape=(2, 5, 3), sigma=0.1, **kw), r, np.zeros((3, 3, 5, 2))))
+    return out
+
+
+@pytest.mark.parametrize("case", _paired_cases(), ids=lambda c: c[0])
+def test_fp16_paired_layout_equals_single_cell_kernels(case):
+    # even nx, x periodic, no mask: the FP16 slots live two cells per word and step with the pair
+    # kernels; store_layout "single" keeps one slot per cell and the one-cell kernels on the same
+    # domain.  Both must give the same populations, psi and moments bit for bit, after odd and
+    # even step counts.
+    name, d, rho, u = case
+    d16 = dict(d, store="fp16")
+    paired = U.run_gpu(d16, rho, u)
+    single = U.run_gpu(dict(d16, store_layout="single"), rho, u)
+    for n in (1, 1, 5):
+        paired.step(n)
+        single.step(n)
+        assert np.array_equal(paired.populations(device=False), single.populations(device=False)), (name, n)
+        assert np.array_equal(paired.psi(device=False), single.psi(device=False)), (name, n)
+        ra, ua, sa = paired.moments(device=False)
+        rb, ub, sb = single.moments(device=False)
+        assert np.array_equal(ra, rb) and np.array_equal(ua, ub) and np.array_equal(sa, sb), (name, n)
+    # a checkpoint restores into either layout
+    f = paired.populations(device=False)
+    single.set_populations(f)
+    paired.set_populations(f)
+    paired.step(3)
+    single.step(3)
+    assert np.array_equal(paired.populations(device=False), single.populations(device=False)), name

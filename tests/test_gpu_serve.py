@@ -108,6 +108,22 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert np.array_equal(a.populations, t.populations)
 
 
+def test_each_result_is_the_same_under_the_aged_srpt_scheduler():
+    # the scheduler advances two of the resident jobs per tick, chosen anew each tick (batches of
+    # alternating pairs come from the engine's cache): every result is still the job's alone
+    from paper_2306_16274_gb300.serve import GpuEngine, Server
+    eng = GpuEngine(batched=True, keep_populations=True, cache=2)
+    mix = Server(eng, budget_bytes=2 ** 33, tick=20, policy="aged_srpt", alpha=1.0, max_batch=2, rate=2e9)
+    together = mix.run(_specs([0.0, 0.0, 0.004, 0.0, 0.002]))
+    assert mix.stats["peak_active"] >= 3 and eng.launch_sets >= 2
+    for spec, t in zip(_specs([0.0] * 5), together):
+        solo = Server(GpuEngine(batched=False, keep_populations=True), budget_bytes=2 ** 33, tick=20)
+        a = solo.run([spec])[0]
+        assert a.status == t.status == "ok"
+        assert (a.steps, a.touch, a.detach, a.contacts, a.sums) == (t.steps, t.touch, t.detach, t.contacts, t.sums)
+        assert np.array_equal(a.populations, t.populations)
+
+
 def test_budget_limits_residency_on_the_gpu():
     from paper_2306_16274_gb300 import estimate_bytes
     from paper_2306_16274_gb300.serve import GpuEngine, Server

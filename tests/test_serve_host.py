@@ -151,3 +151,63 @@ def test_percentiles_and_summary():
     res, srv, _ = serve([job(f"j{k}", 100, 20, arrival=0.001 * k) for k in range(4)], budget=10 ** 9)
     s = summary(res, srv.stats)
     assert s["ok"] == 4 and s["p50_s"] <= s["p99_s"] and s["cell_steps"] == 4 * 100 * 20
+
+
+class WorkEngine(FakeEngine):
+    """A tick costs 1 us per cell advanced plus 0.1 ms, and the widest tick is recorded."""
+
+    def __init__(self, clock, tick):
+        super().__init__(clock, tick)
+        self.widest = 0
+
+    def advance(self, hs, n):
+        for h in hs:
+            h["step"] += n
+        self.widest = max(self.widest, len(hs))
+        self.clock.t += 1e-6 * sum(h["spec"].params.ncell for h in hs) + 1e-4
+
+
+def serve_policy(specs, policy, alpha=1.0, max_batch=2, tick=10):
+    clock = Clock()
+    eng = WorkEngine(clock, tick)
+    srv = Server(eng, 10 ** 12, tick=tick, clock=clock, sleep=clock.sleep, policy=policy, alpha=alpha,
+                 max_batch=max_batch, rate=1e6)
+    return {r.name: r for r in srv.run(specs)}, srv, eng
+
+
+def test_aged_srpt_finishes_a_short_job_first():
+    # a long job is running when a short one arrives: shared evenly ("all") the short job waits on the
+    # long one's work; "aged_srpt" with one job per tick runs it at once and resumes the long one
+    specs = [job("long", 10_000, 1000, detach=False), job("short", 1_000, 100, arrival=0.05, detach=False)]
+    even, _, _ = serve_policy(specs, "all")
+    srpt, _, eng = serve_policy(specs, "aged_srpt", alpha=0.0, max_batch=1)
+    assert eng.widest == 1
+    assert srpt["short"].finished < srpt["long"].finished
+    assert srpt["short"].latency < even["short"].latency
+    assert srpt["short"].latency < 0.11          # its own 10 ticks of 1.1 ms plus at most one tick
+
+
+def test_aging_bounds_the_wait_of_a_long_job():
+    # a long job and a stream of short ones arriving as fast as they are served: pure shortest-first
+    # (alpha = 0) serves every short job first; with aging the long job's priority rises as it waits
+    specs = [job("long", 5_000, 400, detach=False)]
+    specs += [job(f"s{k}", 1_000, 30, arrival=0.002 + 0.0033 * k, detach=False) for k in range(120)]
+    pure, _, _ = serve_policy(specs, "aged_srpt", alpha=0.0, max_batch=1)
+    aged, _, _ = serve_policy(specs, "aged_srpt", alpha=2.0, max_batch=1)
+    assert aged["long"].latency < 0.7 * pure["long"].latency
+
+
+def test_policy_bounds_the_batch_and_keeps_results():
+    specs = [job("a", 100, 200, schedule=[0, 1, 2, 0]), job("b", 5000, 80, arrival=0.002),
+             job("c", 300, 120, schedule=[0, 0, 0, 9, 9, 0], arrival=0.004), job("d", 2000, 60)]
+    ref, _, _ = serve_policy(specs, "all")
+    for k in (1, 2, 3):
+        got, srv, eng = serve_policy(specs, "aged_srpt", max_batch=k)
+        assert eng.widest <= k
+        for name, r in ref.items():
+            g = got[name]
+            assert (g.steps, g.touch, g.detach, g.sums, g.contacts) == (r.steps, r.touch, r.detach, r.sums, r.contacts)
+    with pytest.raises(ValueError):
+        Server(None, 1, policy="lifo")
+    with pytest.raises(ValueError):
+        Server(None, 1, policy="aged_srpt", max_batch=0)
