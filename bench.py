@@ -394,7 +394,60 @@ def serving_specs(n_jobs, rate, seed=2306):
     return specs
 
 
-SERVE_ALPHA, SERVE_BATCH = 1.0, 2
+SERVE_ALPHA, SERVE_BATCH = 4.0, 2
+
+BUDGET_WORKLOAD = ("admission under the memory budget: {n} droplet-on-cylinder impact requests at once (numpy seed "
+                   "2306), edge L ~ U{{96..256}}, height raised to fit cylinder and droplet, R0 = L/6, R/R0 ~ "
+                   "U[0.2, 2], G_ads = 0.23, We = 10, nu = 0.05, C-S 0.7 T_c, lattice by fair coin, {steps} steps "
+                   "each, fields generated per request at admission; budget {budget:.0f} GB")
+
+
+def budget_specs(n_jobs, steps, seed=2306):
+    """Impact requests over the full domain range, all at t = 0, each capped at `steps` steps;
+    make_fields builds a request's fields when the server admits it (host memory stays bounded)."""
+    from paper_2306_16274_gb300 import Params
+    from paper_2306_16274_gb300.serve import JobSpec
+    c = W.constants()["cs"]
+    t = c["T0.7"]
+    rl, rv = t["rho_l"], t["rho_v"]
+    gamma = c["gamma_T0.7"]["kappa0.3"]
+    eos = dict(eos="cs", eos_p=(c["a"], c["b"], c["R"], t["T"]), G=-1.0, sigma=0.1)
+    specs = []
+    for j in W.serving_jobs(n_jobs, 0.0, seed=seed, edge=(96, 256), impact_fraction=1.0):
+        R0 = j["R0"]
+        U = (10.0 * gamma / (rl * R0)) ** 0.5
+        p = Params(lattice=j["lattice"], shape=j["shape"], bc=("periodic", "periodic", "wall"), kappa=0.3,
+                   G_ads=0.23, rates={"s2": 1.0 / (3 * 0.05 + 0.5)}, **eos)
+
+        def make(j=j, R0=R0, U=U):
+            rho, u, solid = W.cylinder_impact(j["shape"], R0, j["Rc"], rl, rv, U, gap=3.0, W=3.0)
+            return rho.astype(np.float32), u.astype(np.float32), solid
+
+        specs.append(JobSpec(name=j["name"], params=p, make_fields=make, steps=steps, arrival=0.0, has_solid=True))
+    return specs
+
+
+def run_serving_budget(n_jobs=320, steps=200, budget=150e9):
+    """More impact requests over the full domain range than the budget holds, all at once, batched
+    (every resident job each tick): the budget, not the slot count, bounds the resident set."""
+    import torch
+
+    from paper_2306_16274_gb300 import estimate_bytes
+    from paper_2306_16274_gb300.serve import GpuEngine, Server, summary
+    specs = budget_specs(n_jobs, steps)
+    need = sum(estimate_bytes(s.params, s.has_solid) for s in specs)
+    eng = GpuEngine(batched=True)
+    srv = Server(eng, budget, tick=100, max_active=10 ** 6)
+    res = srv.run(specs)
+    eng.close()
+    torch.cuda.synchronize()
+    out = summary(res, srv.stats)
+    cells = [int(np.prod(s.params.shape)) for s in specs]
+    return {"workload": BUDGET_WORKLOAD.format(n=n_jobs, steps=steps, budget=budget / 1e9), "jobs": n_jobs,
+            "requested_bytes": need, "budget_bytes": budget, "peak_bytes": out["peak_bytes"],
+            "peak_active": out["peak_active"], "cells_min": min(cells), "cells_max": max(cells),
+            "mlups_busy": out["mlups_busy"], "mlups_wall": out["mlups_wall"], "busy_s": out["busy_s"],
+            "wall_s": out["wall_s"], "ok": out["ok"], "failed": [r.name + ": " + r.status for r in res if r.status != "ok"]}
 
 
 def run_serving(n_jobs=64, load=0.8, tick=100, budget=150e9):
@@ -580,6 +633,8 @@ def main():
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-onepass", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=64)
+    ap.add_argument("--serving-budget", action="store_true",
+                    help="also run the admission leg over the full domain range (minutes of host-side field generation)")
     ap.add_argument("--temperature", default="0.6", choices=["0.6", "0.7"],
                     help="T / T_c of the C-S EOS; 0.7 only for profiling cases")
     ap.add_argument("--size", type=int, default=256,
@@ -622,6 +677,7 @@ def main():
                                    for Q in ((19,) if args.no_q27 else (19, 27))}
     batched = None if (args.no_batched or not single or SHAPE != (256, 256, 256)) else run_batched(args.batched_steps)
     serving = None if (args.no_serving or not single or SHAPE != (256, 256, 256)) else run_serving(args.serving_jobs)
+    budget_leg = run_serving_budget() if (args.serving_budget and single) else None
     if rank != 0:
         return
     ab = algorithmic_bytes(19)
@@ -691,6 +747,8 @@ def main():
                 "mass_drift_rel": r["mass_drift"], "device_bytes": r["device_bytes"]}
     if batched:
         line["batched"] = batched
+    if budget_leg:
+        line["serving_budget"] = budget_leg
     if serving:
         line["serving"] = serving
         po = serving.get("poisson", {})

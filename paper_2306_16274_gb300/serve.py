@@ -98,7 +98,7 @@ class Server:
     POLICIES = ("all", "aged_srpt")
 
     def __init__(self, engine, budget_bytes, tick=100, max_active=64, clock=time.perf_counter, sleep=time.sleep,
-                 policy="all", alpha=1.0, max_batch=2, rate=1.6e10):
+                 policy="all", alpha=4.0, max_batch=2, rate=1.6e10):
         if tick < 2 or tick % 2:
             raise ValueError("tick must be an even number of steps >= 2")
         if max_active < 1:
