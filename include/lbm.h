@@ -125,7 +125,10 @@ typedef struct {
                             /* demand for lbm_get_psi / lbm_get_moments); same results bit   */
                             /* for bit, twice the population memory.  Periodic boundaries,   */
                             /* no solid mask, FP32 store; cannot join a batch.  0: the       */
-                            /* in-place two-pass step (default).                             */
+                            /* in-place two-pass step (default).  2 (LBM_ONEPASS_STAGED):    */
+                            /* the one-pass step with each plane's populations staged in     */
+                            /* shared memory by tensor copies (nx a multiple of 32, ny of 4; */
+                            /* see lbm_staged_copies).                                       */
     int32_t store_layout;   /* FP16 store only.  LBM_LAYOUT_AUTO (0, default): when nx is    */
                             /* even, x is periodic and no solid mask is given, one 4-byte    */
                             /* word holds the slots of cells x and x + nx/2 and each thread  */
@@ -134,6 +137,7 @@ typedef struct {
                             /* the same bit for bit; the layout changes speed only.          */
 } lbm_params;
 
+#define LBM_ONEPASS_STAGED 2
 #define LBM_LAYOUT_AUTO 0
 #define LBM_LAYOUT_SINGLE 1
 
@@ -344,6 +348,21 @@ const char* lbm_status_string(lbm_status s);
  * made.  Returns the count since the library was loaded, on the current device; 0 in the normal
  * build, where the checks are compiled away. */
 uint64_t lbm_debug_bounds_violations(void);
+
+/* Staged one-pass step (the paper has no counterpart; a data-movement choice).  A context created
+ * with onepass = LBM_ONEPASS_STAGED (nx a multiple of 32, ny of 4) stages, for every z plane a
+ * block needs, the pulled populations of its 32 x 4 tile and one-cell border in shared memory with
+ * one tensor copy (TMA) per population; the results are those of the other steps bit for bit.  It
+ * measured slower than the unstaged one-pass step on one GB300 (256^3: D3Q19 1.00 against 0.68 ms).
+ * lbm_staged_copies returns 1 for such a context, 0 otherwise (or for NULL).
+ * Every wait of the kernel on its copies is bounded in time (about 2 s); past the limit the block
+ * abandons the step, the status word records it and the next lbm_sync / lbm_get_moments returns
+ * LBM_ERR_TIMEOUT (sticky until the next lbm_init_fields or lbm_set_populations).
+ * lbm_debug_stage_timeout(ctx, 1) makes every later staged step expect more bytes than its copies
+ * deliver, with a wait limit of about 10 ms, so that the timeout path can be tested; (ctx, 0)
+ * restores normal steps.  LBM_ERR_STATE if ctx does not stage. */
+int32_t lbm_staged_copies(const lbm_ctx* ctx);
+lbm_status lbm_debug_stage_timeout(lbm_ctx* ctx, int32_t enable);
 
 #ifdef __cplusplus
 }

@@ -69,7 +69,11 @@ lbm_status validate(const lbm_params* p, std::string& why) {
         why = "store must be LBM_STORE_FP32 or LBM_STORE_FP16";
         return LBM_ERR_ARG;
     }
-    if (p->onepass != 0 && p->onepass != 1) { why = "onepass must be 0 or 1"; return LBM_ERR_ARG; }
+    if (p->onepass < 0 || p->onepass > 2) { why = "onepass must be 0, 1 or 2 (LBM_ONEPASS_STAGED)"; return LBM_ERR_ARG; }
+    if (p->onepass == 2 && (p->nx % 32 != 0 || p->ny % 4 != 0)) {
+        why = "onepass = 2 (staged) needs nx a multiple of 32 and ny a multiple of 4";
+        return LBM_ERR_ARG;
+    }
     if (p->store_layout != LBM_LAYOUT_AUTO && p->store_layout != LBM_LAYOUT_SINGLE) {
         why = "store_layout must be LBM_LAYOUT_AUTO or LBM_LAYOUT_SINGLE";
         return LBM_ERR_ARG;
@@ -198,10 +202,60 @@ cudaError_t run_psi(lbm_ctx* c) {
                       : lbm::launch_psi_q27(c->kp, c->parity, s, bufs(c), c->stream);
 }
 
+// Tensor map of one population copy for the staged one-pass kernel: a 4-D array (x, y, z,
+// population) of floats, boxes of 40 x 8 x 1 x 1 (plane strides are multiples of 256 bytes; rows of
+// nx floats with nx a multiple of 32).  The encoder is taken from the driver through the runtime, so
+// the library links no driver library.
+bool encode_copy_map(CUtensorMap* m, const void* base, const KParams& k, int Q) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<Encode>(fn);
+    }();
+    if (!encode) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)k.nx, (cuuint64_t)k.ny, (cuuint64_t)k.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)k.nx * 4, (cuuint64_t)k.nx * k.ny * 4, (cuuint64_t)k.plane * 4};
+    const cuuint32_t box[4] = {40, 8, 1, 1};
+    const cuuint32_t step[4] = {1, 1, 1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, step,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// onepass = 2: staged copies (full 32 x 4 tiles, so every box starts on a 16-byte boundary); one
+// tensor map per population copy.  False if the driver cannot encode them.
+bool setup_staging(lbm_ctx* c) {
+    const void* copies[2] = {c->f, c->f2};
+    for (int k = 0; k < 2; ++k) {
+        if (!encode_copy_map(&c->tmap[k], copies[k], c->kp, c->Q)) return false;
+        c->tmap_base[k] = copies[k];
+    }
+    c->staged = 1;
+    return true;
+}
+
 // one-pass layout: one launch per step, then the copies trade places
 cudaError_t run_onepass(lbm_ctx* c) {
-    cudaError_t e = c->Q == 19 ? lbm::launch_onepass_q19(c->kp, c->status, c->stream)
-                               : lbm::launch_onepass_q27(c->kp, c->status, c->stream);
+    cudaError_t e;
+    if (c->staged) {
+        const int k = c->tmap_base[0] == c->f ? 0 : 1;      // the copy this step reads
+        // waits on staged copies give up after ~2 s (2^32 cycles); the timeout test uses ~10 ms and
+        // expects bytes that no copy delivers
+        const unsigned extra = c->stage_timeout_test ? 4096u : 0u;
+        const long long cycles = c->stage_timeout_test ? 20000000LL : 4294967296LL;
+        e = c->Q == 19 ? lbm::launch_onepass_tma_q19(c->kp, c->tmap[k], c->status, extra, cycles, c->stream)
+                       : lbm::launch_onepass_tma_q27(c->kp, c->tmap[k], c->status, extra, cycles, c->stream);
+    } else {
+        e = c->Q == 19 ? lbm::launch_onepass_q19(c->kp, c->status, c->stream)
+                       : lbm::launch_onepass_q27(c->kp, c->status, c->stream);
+    }
     std::swap(c->f, c->f2);
     for (int i = 0; i < 27; ++i) std::swap(c->kp.fq[i], c->kp.gq[i]);
     return e;
@@ -273,7 +327,10 @@ lbm_status read_status(lbm_ctx* c) {
     CK(c, cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (c->sticky == LBM_OK) {
-        if (st & lbm::ST_UNSTABLE) {
+        if (st & lbm::ST_TIMEOUT) {
+            c->sticky = LBM_ERR_TIMEOUT;
+            c->err = "a wait for populations staged by tensor copies ran out of time (the step was abandoned)";
+        } else if (st & lbm::ST_UNSTABLE) {
             c->sticky = LBM_ERR_UNSTABLE;
             c->err = "non-finite or non-positive density on a fluid cell";
         } else if (st & lbm::ST_EOS_RANGE) {
@@ -369,12 +426,13 @@ lbm_status lbm_create(const lbm_params* params, void* cuda_stream, lbm_ctx** out
         for (int i = 0; i < c->Q; ++i)
             c->kp.fq[i] = reinterpret_cast<float*>(reinterpret_cast<char*>(c->f) + (size_t)i * plane * esize);
     for (int k = 0; k < 2 && c->f16 && e == cudaSuccess; ++k) e = alloc((void**)&c->rbuf[k], (size_t)n * sizeof(float));
-    c->onepass = params->onepass;
+    c->onepass = params->onepass != 0;
     if (c->onepass && e == cudaSuccess) {
         e = alloc((void**)&c->f2, (size_t)c->Q * plane * sizeof(float));
         if (e == cudaSuccess)
             for (int i = 0; i < c->Q; ++i) c->kp.gq[i] = c->f2 + (size_t)i * plane;
     }
+    if (params->onepass == 2 && e == cudaSuccess && !setup_staging(c)) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = alloc((void**)&c->psi, (size_t)n * sizeof(float));
     if (e == cudaSuccess) e = alloc((void**)&c->status, 64);
     if (e == cudaSuccess) e = alloc((void**)&c->partials, (size_t)c->partial_blocks * 4 * sizeof(double));
@@ -669,6 +727,15 @@ const char* lbm_last_error(const lbm_ctx* c) {
     if (!c) return g_create_error.c_str();
     return c->err.c_str();
 }
+
+lbm_status lbm_debug_stage_timeout(lbm_ctx* c, int32_t enable) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->staged) return fail(c, LBM_ERR_STATE, "this context does not stage populations with tensor copies");
+    c->stage_timeout_test = enable != 0;
+    return LBM_OK;
+}
+
+int32_t lbm_staged_copies(const lbm_ctx* c) { return c ? c->staged : 0; }
 
 uint64_t lbm_debug_bounds_violations(void) {
     return lbm::bounds_violations_q19() + lbm::bounds_violations_q27();

@@ -20,6 +20,12 @@ struct lbm_ctx {
     int paired = 0;              // f16 slots in the x-paired layout (see KParams::paired)
     int onepass = 0;             // one-pass layout: f is the copy being read, f2 the one written
     float* f2 = nullptr;
+    // one-pass contexts with full 32 x 4 tiles stage each plane's populations with tensor copies:
+    // one tensor map per population copy (tmap_base[k] is the copy tmap[k] describes)
+    int staged = 0;
+    CUtensorMap tmap[2];
+    const void* tmap_base[2] = {nullptr, nullptr};
+    int stage_timeout_test = 0;  // lbm_debug_stage_timeout
     float* rbuf[2] = {nullptr, nullptr};   // f16: density fields, see bufs() in capi.cu
     int rs = 0;
     float* psi = nullptr;        // ncell floats

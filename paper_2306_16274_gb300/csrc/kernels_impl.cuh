@@ -732,6 +732,224 @@ __global__ void __launch_bounds__(32 * BY, MINB) collide_onepass_kernel(const KP
     }
 }
 
+// ---- one-pass step with the pulled populations staged by TMA (full 32 x 4 tiles: nx a multiple of
+// 32, ny of 4).  For every plane c a block needs, one tensor copy per population i brings the slots of
+// storage plane c - e_iz for x0 - 4 .. x0 + 35 and y0 - 2 .. y0 + 5 (a 40 x 8 box; starting at x0 - 4
+// keeps every copy on a 16-byte boundary) into shared memory, where the block's cells and its one-cell
+// border read their pulled populations (population i of cell x is slot i of x - e_i).  Two box sets
+// alternate: the copies for plane c + 2 are issued as soon as plane c has been consumed, so they land
+// while plane c - 1 is collided and no thread waits on a load of its own.  Box positions outside the
+// domain come back as zeros; the tiles at the x and y faces fill their periodic images from global
+// memory.  The arithmetic and its order are those of collide_onepass_kernel, so the results are the
+// same bit for bit.  Every wait on a copy is bounded in time: past `wait_cycles` the whole block
+// raises ST_TIMEOUT, waits (bounded again) for its copies still in flight and returns.
+constexpr int OT_HX = 40, OT_HY = 8, OT_BOX = OT_HX * OT_HY;
+constexpr int OT_RX = 34, OT_RY = 6, OT_RP = OT_RX * OT_RY, OT_HALO = 2 * OT_RX + 2 * 4;
+constexpr int OT_MINB = LBM_Q == 19 ? 4 : 3;
+
+struct OtShared {
+    float pop[2][Q][OT_BOX];     // two box sets, one box per population
+    float ring[4][OT_RP];        // psi of planes z-1, z, z+1 (and the next)
+    unsigned long long bar[2];   // completion of each box set's copies
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// one thread: the copies of plane c into box set b, completing on bar[b] (extra: bytes expected
+// beyond those the copies deliver -- nonzero only to exercise the timeout path)
+__device__ __forceinline__ void ot_issue(OtShared& sm, int b, const CUtensorMap* map, int x0, int y0, int c, int nz,
+                                         unsigned extra) {
+    const uint32_t bar = smem_u32(&sm.bar[b]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"((unsigned)(Q * OT_BOX * sizeof(float)) + extra) : "memory");
+    const int cw = wrap1(c, nz);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int pz = wrap1(cw - EZ(i), nz);
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+            :: "r"(smem_u32(&sm.pop[b][i][0])), "l"(reinterpret_cast<uint64_t>(map)), "r"(x0 - 4), "r"(y0 - 2), "r"(pz),
+               "r"(i), "r"(bar)
+            : "memory");
+    }
+}
+
+// bounded wait for phase `ph` of bar[b]; false once wait_cycles have passed
+__device__ __forceinline__ bool ot_wait(OtShared& sm, int b, unsigned ph, long long wait_cycles) {
+    const uint32_t bar = smem_u32(&sm.bar[b]);
+    const long long t0 = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok) : "r"(bar), "r"(ph) : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > wait_cycles) return false;
+    }
+}
+
+// Plane c from box set b: wait for its copies (bounded), fill the periodic images at the faces, then psi
+// of the tile and of its border into `slot`; the own cell's pulled populations into p.  False if the
+// wait ran out on any thread of the block (the decision is block-wide).
+template <bool MULTIPHASE>
+__device__ __forceinline__ bool ot_stage(const KParams& kp, OtShared& sm, int c, int b, float* slot, float (&p)[Q],
+                                         unsigned& phase, unsigned& pending, long long wait_cycles, unsigned* status,
+                                         int tid, int x0, int y0, bool face, int lc, bool has_halo, int rx, int ry,
+                                         int hl) {
+    const int tx = tid & 31, ty = tid >> 5;
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    const bool ok = ot_wait(sm, b, (phase >> b) & 1u, wait_cycles);
+    if (__syncthreads_or(!ok)) return false;
+    phase ^= 1u << b;
+    pending &= ~(1u << b);
+    if (face) {
+        // positions outside [0, nx) x [0, ny) among the needed x0-2 .. x0+33, y0-2 .. y0+5
+        const int nL = x0 == 0, nR = x0 + 32 == nx, nT = y0 == 0, nB = y0 + 4 == ny;
+        const int per = 16 * nL + 16 * nR + 72 * nT + 72 * nB;
+        const int cw = wrap1(c, nz);
+        for (int k = tid; k < Q * per; k += 128) {
+            const int i = k % Q;
+            int r = k / Q, lx, ly;
+            if (nL && r < 16) { lx = 2 + (r & 1); ly = r >> 1; }
+            else {
+                r -= 16 * nL;
+                if (nR && r < 16) { lx = 36 + (r & 1); ly = r >> 1; }
+                else {
+                    r -= 16 * nR;
+                    if (nT && r < 72) { lx = 2 + r % 36; ly = r / 36; }
+                    else { r -= 72 * nT; lx = 2 + r % 36; ly = 6 + r / 36; }
+                }
+            }
+            int gx = x0 - 4 + lx, gy = y0 - 2 + ly;
+            gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+            gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+            // population i's plane base and storage plane c - e_iz, selected with compile-time indices
+            const float* src = kp.fq[0];
+            int pz = cw;
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (q == i) {
+                    src = kp.fq[q];
+                    pz = wrap1(cw - EZ(q), nz);
+                }
+            sm.pop[b][i][ly * OT_HX + lx] =
+                __ldg(src + bounded((uint32_t)pz * nxy + (uint32_t)gy * (uint32_t)nx + (uint32_t)gx,
+                                    (unsigned long long)kp.ncell));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) p[i] = sm.pop[b][i][(ty + 2 - EY(i)) * OT_HX + (tx + 4 - EX(i))];
+    if (MULTIPHASE) {
+        float rho = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += p[i];
+        slot[lc] = eval_psi(kp, rho, status);
+        if (has_halo) {
+            float rh = 0.0f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) rh += sm.pop[b][i][(ry + 1 - EY(i)) * OT_HX + (rx + 3 - EX(i))];
+            slot[hl] = eval_psi(kp, rh, status);
+        }
+    }
+    __syncthreads();   // the box set has been read; psi of plane c is in the ring
+    return true;
+}
+
+// after a wait ran out: raise ST_TIMEOUT and wait (bounded again) for the copies still in flight
+__device__ __forceinline__ void ot_bail(OtShared& sm, unsigned phase, unsigned pending, long long wait_cycles,
+                                        unsigned* status, int tid) {
+    if (tid == 0) atomicOr(status, ST_TIMEOUT);
+    for (int b = 0; b < 2; ++b)
+        if ((pending >> b) & 1u) (void)ot_wait(sm, b, (phase >> b) & 1u, wait_cycles);
+}
+
+template <bool MULTIPHASE>
+__global__ void __launch_bounds__(128, OT_MINB) collide_onepass_tma_kernel(const KParams kp,
+                                                                          const __grid_constant__ CUtensorMap map,
+                                                                          unsigned* status, int zchunk,
+                                                                          unsigned extra_tx, long long wait_cycles) {
+    extern __shared__ __align__(128) unsigned char ot_raw[];
+    OtShared& sm = *reinterpret_cast<OtShared*>(ot_raw);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 4, z0 = blockIdx.z * zchunk;
+    const int nx = kp.nx, ny = kp.ny, nz = kp.nz;
+    const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
+    const int zend = min(z0 + zchunk, nz);
+    const int base = z0 - 1;                        // first plane staged (psi only)
+    const bool face = x0 == 0 || x0 + 32 == nx || y0 == 0 || y0 + 4 == ny;
+    const int lc = (ty + 1) * OT_RX + tx + 1;
+    const uint32_t own = (uint32_t)(y0 + ty) * (uint32_t)nx + (uint32_t)(x0 + tx);
+    // one border cell of the ring plane for 19 lanes of each warp (as collide_onepass_kernel)
+    constexpr int PER_WARP = (OT_HALO + 3) / 4;
+    const int hb = (tid & 31) < PER_WARP ? (tid >> 5) * PER_WARP + (tid & 31) : OT_HALO;
+    const bool has_halo = MULTIPHASE && hb < OT_HALO;
+    int rx = 0, ry = 0;
+    if (has_halo) {
+        if (hb < OT_RX) { rx = hb; ry = 0; }
+        else if (hb < 2 * OT_RX) { rx = hb - OT_RX; ry = OT_RY - 1; }
+        else if (hb < 2 * OT_RX + 4) { rx = 0; ry = 1 + hb - 2 * OT_RX; }
+        else { rx = OT_RX - 1; ry = 1 + hb - 2 * OT_RX - 4; }
+    }
+    const int hl = ry * OT_RX + rx;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&sm.bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned phase = 0u;     // bit b: the completion phase box set b waits for next
+    unsigned pending = 3u;   // bit b: box set b has copies in flight
+    if (tid == 0) {
+        ot_issue(sm, 0, &map, x0, y0, base, nz, extra_tx);
+        ot_issue(sm, 1, &map, x0, y0, base + 1, nz, extra_tx);
+    }
+
+    float pn[Q];
+    {
+        float tmp[Q];
+        if (!ot_stage<MULTIPHASE>(kp, sm, base, 0, sm.ring[0], tmp, phase, pending, wait_cycles, status, tid, x0, y0, face,
+                                  lc, has_halo, rx, ry, hl))
+            return ot_bail(sm, phase, pending, wait_cycles, status, tid);
+    }
+    if (tid == 0 && base + 2 <= zend) ot_issue(sm, 0, &map, x0, y0, base + 2, nz, extra_tx);
+    if (base + 2 <= zend) pending |= 1u;
+    if (!ot_stage<MULTIPHASE>(kp, sm, z0, 1, sm.ring[1], pn, phase, pending, wait_cycles, status, tid, x0, y0, face, lc,
+                              has_halo, rx, ry, hl))
+        return ot_bail(sm, phase, pending, wait_cycles, status, tid);
+    if (tid == 0 && base + 3 <= zend) ot_issue(sm, 1, &map, x0, y0, base + 3, nz, extra_tx);
+    if (base + 3 <= zend) pending |= 2u;
+    for (int z = z0, j = 0; z < zend; ++z, ++j) {
+        float p[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) p[i] = pn[i];
+        const int c = z + 1, b = (c - base) & 1;
+        if (!ot_stage<MULTIPHASE>(kp, sm, c, b, sm.ring[(j + 2) & 3], pn, phase, pending, wait_cycles, status, tid, x0,
+                                  y0, face, lc, has_halo, rx, ry, hl))
+            return ot_bail(sm, phase, pending, wait_cycles, status, tid);
+        if (tid == 0 && c + 2 <= zend) ot_issue(sm, b, &map, x0, y0, c + 2, nz, extra_tx);
+        if (c + 2 <= zend) pending |= 1u << b;
+        Forces Fo;
+        if (MULTIPHASE) {
+            Fo = stencil_forces3<Q, false>(kp, &sm.ring[j & 3][lc], &sm.ring[(j + 1) & 3][lc],
+                                           &sm.ring[(j + 2) & 3][lc], OT_RX, 0u);
+        } else {
+            Fo.fx = Fo.fy = Fo.fz = 0.f;
+            Fo.qxx = Fo.qyy = Fo.qzz = Fo.qxy = Fo.qxz = Fo.qyz = 0.f;
+            Fo.s2 = 0.f;
+        }
+        float rho, ux, uy, uz;
+        collide<Q>(kp, p, Fo, rho, ux, uy, uz);
+        if (!(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 1e30f)) atomicOr(status, ST_UNSTABLE);
+        const uint32_t cell = (uint32_t)z * nxy + own;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) kp.gq[i][bounded(cell, (unsigned long long)kp.ncell)] = p[i];
+    }
+}
+
 // natural-order populations (plane i at fin + i * fstride) -> one-pass layout (slot i of x - e_i)
 __global__ void pull_store_kernel(KParams kp, const float* __restrict__ fin, long long fstride,
                                   float* __restrict__ fout) {
@@ -1275,6 +1493,32 @@ cudaError_t LBM_CAT(launch_contact_q, LBM_Q)(const KParams& kp, int parity, cons
 // one-pass tiles: 32 x 4 cells (the 76-cell border fits the 128 threads), 7 (D3Q19) / 5 (D3Q27)
 // blocks per SM -- the best of 32 x 4 / 8 / 16 tiles and 4-8 blocks per SM, measured
 constexpr int OP_BY = 4, OP_MINB = LBM_Q == 19 ? 7 : 5;
+
+cudaError_t LBM_CAT(launch_onepass_tma_q, LBM_Q)(const KParams& kp, const CUtensorMap& read_map, unsigned* status,
+                                                 unsigned extra_tx, long long wait_cycles, cudaStream_t st) {
+    // two staged planes at a chunk's start
+    const int zc = choose_zchunk(kp, 2.0, kp.nz, 4, OT_MINB);
+    const dim3 g(kp.nx / 32, kp.ny / 4, (kp.nz + zc - 1) / zc), b(32, 4);
+    const size_t smem = sizeof(OtShared);
+    static bool configured[2] = {false, false};
+    cudaError_t e = cudaSuccess;
+    if (kp.multiphase) {
+        if (!configured[1]) {
+            e = cudaFuncSetAttribute(collide_onepass_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            configured[1] = e == cudaSuccess;
+        }
+        if (e == cudaSuccess)
+            collide_onepass_tma_kernel<true><<<g, b, smem, st>>>(kp, read_map, status, zc, extra_tx, wait_cycles);
+    } else {
+        if (!configured[0]) {
+            e = cudaFuncSetAttribute(collide_onepass_tma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            configured[0] = e == cudaSuccess;
+        }
+        if (e == cudaSuccess)
+            collide_onepass_tma_kernel<false><<<g, b, smem, st>>>(kp, read_map, status, zc, extra_tx, wait_cycles);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
 
 cudaError_t LBM_CAT(launch_onepass_q, LBM_Q)(const KParams& kp, unsigned* status, cudaStream_t st) {
     // a chunk starts with two psi planes whose loads nothing overlaps

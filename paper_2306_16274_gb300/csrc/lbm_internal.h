@@ -2,13 +2,14 @@
 // translation units (kernels_q19.cu, kernels_q27.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbm {
 
 // Status bits raised by kernels (read by lbm_sync).
-enum : unsigned { ST_UNSTABLE = 1u, ST_EOS_RANGE = 2u };
+enum : unsigned { ST_UNSTABLE = 1u, ST_EOS_RANGE = 2u, ST_TIMEOUT = 4u };
 
 // Everything a kernel needs, flattened to floats on the host (derived terms
 // precomputed in double, rounded once).
@@ -124,6 +125,8 @@ struct Bufs {
     cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const Bufs& B, float thr, int* out, \
                                     cudaStream_t st);                                               \
     cudaError_t launch_onepass_q##Q(const KParams& kp, unsigned* status, cudaStream_t st);          \
+    cudaError_t launch_onepass_tma_q##Q(const KParams& kp, const CUtensorMap& read_map, unsigned* status, \
+                                        unsigned extra_tx, long long wait_cycles, cudaStream_t st);       \
     cudaError_t launch_pull_store_q##Q(const KParams& kp, const float* fin, long long fstride,       \
                                        float* fout, cudaStream_t st);                               \
     unsigned long long bounds_violations_q##Q();

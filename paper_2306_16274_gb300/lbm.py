@@ -88,6 +88,8 @@ def lib():
         "lbm_batch_destroy": (V, [P]),
         "lbm_batch_last_error": (ctypes.c_char_p, [P]),
         "lbm_debug_bounds_violations": (ctypes.c_uint64, []),
+        "lbm_staged_copies": (I32, [P]),
+        "lbm_debug_stage_timeout": (I32, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -103,7 +105,8 @@ class Params:
     eos "none" / "cs" (eos_p = a, b, R, T) / "piecewise" (rho1, rho2, theta_v, theta_m, theta_l);
     rates: s0 .. s6 of Eq. e12 (defaults from the paper, filled in by the library);
     store "fp32" or "fp16" (shifted FP16 population store); onepass: one pass per step over two
-    population copies (periodic, no solids, FP32); store_layout "auto" (FP16 slots of cells x and
+    population copies (periodic, no solids, FP32), or "staged" for the same step with each plane's
+    populations staged by tensor copies (nx a multiple of 32, ny of 4); store_layout "auto" (FP16 slots of cells x and
     x + nx/2 share a word where nx is even, x periodic and no mask is given) or "single"."""
     lattice: int = 19
     shape: tuple = (32, 32, 32)
@@ -149,7 +152,7 @@ class Params:
         c.psi_ext_rho = float(self.psi_ext_rho)
         c.zchunk = int(self.zchunk)
         c.store = STORE[self.store] if isinstance(self.store, str) else int(self.store)
-        c.onepass = 1 if self.onepass else 0
+        c.onepass = 2 if self.onepass == "staged" else (1 if self.onepass else 0)
         c.store_layout = LAYOUT[self.store_layout] if isinstance(self.store_layout, str) else int(self.store_layout)
         return c
 
@@ -358,6 +361,15 @@ class Simulation:
         n = (ctypes.c_int64 * 2)()
         self._check(self._L.lbm_get_kernel_timing(self._ctx, ms, n))
         return {"psi": ms[0], "collide": ms[1]}, {"psi": n[0], "collide": n[1]}
+
+    @property
+    def staged(self):
+        """True when the one-pass step stages populations with tensor copies (lbm_staged_copies)."""
+        return bool(self._L.lbm_staged_copies(self._ctx))
+
+    def debug_stage_timeout(self, enable=True):
+        """lbm_debug_stage_timeout: make the staged step's waits run out (to test the timeout path)."""
+        self._check(self._L.lbm_debug_stage_timeout(self._ctx, 1 if enable else 0))
 
     @property
     def step_count(self):

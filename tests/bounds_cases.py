@@ -30,6 +30,10 @@ def main():
         d = dict(lattice=Q, shape=shape, sigma=0.1, kappa=0.3, zchunk=5, **kw)
         out[f"periodic{Q}"] = digest(U.run_gpu(d, rho, u, steps=7))
         out[f"onepass{Q}"] = digest(U.run_gpu(dict(d, onepass=True), rho, u, steps=7))
+        # the one-pass step with tensor-copy staging and face images (nx a multiple of 32, ny of 4)
+        ss = (64, 12, 9)
+        rs, us = W.droplet(ss, 4.0, rl, rv, W=3.0)
+        out[f"onepass_staged{Q}"] = digest(U.run_gpu(dict(d, shape=ss, onepass="staged"), rs, us, steps=7))
         out[f"fp16_{Q}"] = digest(U.run_gpu(dict(d, store="fp16"), rho, u, steps=7))
         # even nx: the x-paired FP16 layout and its pair kernels, periodic and with y / z walls
         sp = (34, 30, 28)

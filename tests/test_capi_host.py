@@ -149,12 +149,16 @@ def test_estimate_bytes_fp16_store(lib):
         assert L.estimate_bytes(L.Params(lattice=Q, shape=(nx, ny, nz), store="fp16")) == want
 
 
-def test_onepass_flag_must_be_0_or_1(lib):
+def test_onepass_flag_must_be_0_1_or_2(lib):
     c = L.Params(lattice=19, shape=(4, 4, 4)).to_c()
-    c.onepass = 2
+    c.onepass = 3
     ctx = ctypes.c_void_p()
     assert lib.lbm_create(ctypes.byref(c), None, ctypes.byref(ctx)) == 1 and not ctx.value
     assert b"onepass" in lib.lbm_last_error(None)
+    # the staged one-pass step needs full 32 x 4 tiles
+    c.onepass = 2
+    assert lib.lbm_create(ctypes.byref(c), None, ctypes.byref(ctx)) == 1 and not ctx.value
+    assert b"multiple of 32" in lib.lbm_last_error(None)
 
 
 def test_estimate_bytes_onepass_holds_two_population_copies(lib):

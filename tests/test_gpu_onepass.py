@@ -141,3 +141,62 @@ def test_onepass_degenerate_extents(Q, shape):
     a = U.run_gpu(d, rho, u, steps=5)
     b = U.run_gpu(dict(d, onepass=True), rho, u, steps=5)
     assert np.array_equal(a.populations(device=False), b.populations(device=False))
+
+
+def _staged_cases():
+    kw7, rl7, rv7 = U.cs_eos("T0.7")
+    out = []
+    shape = (64, 12, 9)        # two tiles in x (both at a face), three in y, z-chunks of 3 planes
+    out.append(("drop19_64x12", dict(lattice=19, shape=shape, sigma=0.1, kappa=0.3, zchunk=3, g=(1e-5, 0.0, 0.0),
+                                     **kw7), *W.droplet(shape, 4.0, rl7, rv7, W=3.0)))
+    shape = (96, 16, 7)        # a tile away from the x faces
+    out.append(("drop27_96x16", dict(lattice=27, shape=shape, sigma=0.1, zchunk=4, **kw7),
+                *W.droplet(shape, 5.0, rl7, rv7, W=3.0)))
+    shape = (32, 4, 5)         # one tile: all four faces at once
+    out.append(("single19_32x4", dict(lattice=19, shape=shape, rates={"s2": 1.3}), *W.perturbed(shape, seed=5)))
+    shape = (32, 8, 1)         # one plane: every staged plane is the same storage plane
+    out.append(("single27_nz1", dict(lattice=27, shape=shape, g=(0.0, 2e-5, 0.0)), *W.perturbed(shape, seed=6)))
+    return out
+
+
+@pytest.mark.parametrize("case", _staged_cases(), ids=lambda c: c[0])
+def test_staged_onepass_is_bitwise_equal_to_two_pass(case):
+    # onepass = "staged" (nx a multiple of 32, ny of 4): the one-pass step stages each plane's pulled
+    # populations with tensor copies (TMA) and fills the periodic images at the faces; results equal
+    # the two-pass step
+    name, d, rho, u = case
+    a = U.run_gpu(d, rho, u, steps=0)
+    b = U.run_gpu(dict(d, onepass="staged"), rho, u, steps=0)
+    assert b.staged
+    for n in (1, 6, 21):
+        a.step(n)
+        b.step(n)
+        fa, fb = a.populations(device=False), b.populations(device=False)
+        assert np.array_equal(fa, fb), (name, n, float(np.abs(fa - fb).max()))
+        ra, ua, sa = a.moments(device=False)
+        rb, ub, sb = b.moments(device=False)
+        assert np.array_equal(ra, rb) and np.array_equal(ua, ub) and list(sa) == list(sb)
+
+
+def test_staged_copy_waits_are_bounded():
+    # a staged step that expects more bytes than its copies deliver: every wait runs out (about
+    # 10 ms), the blocks abandon the step and LBM_ERR_TIMEOUT is reported; the context stays usable
+    from paper_2306_16274_gb300 import LBMError
+    name, d, rho, u = _staged_cases()[0]
+    sim = U.run_gpu(dict(d, onepass="staged"), rho, u, steps=2)
+    sim.debug_stage_timeout(True)
+    sim.step(1)
+    with pytest.raises(LBMError) as e:
+        sim.sync()
+    assert e.value.status == 6
+    sim.debug_stage_timeout(False)
+    ref = U.run_gpu(d, rho, u, steps=3)
+    sim.init_fields(rho.astype(np.float32), u.astype(np.float32))
+    sim.step(3)
+    sim.sync()
+    assert np.array_equal(sim.populations(device=False), ref.populations(device=False))
+    # contexts that do not stage refuse the switch
+    plain = U.run_gpu(dict(lattice=19, shape=(64, 8, 4), onepass=True), *W.perturbed((64, 8, 4), seed=1))
+    assert not plain.staged
+    with pytest.raises(LBMError):
+        plain.debug_stage_timeout(True)
