@@ -395,10 +395,11 @@ __device__ __forceinline__ void pair_offsets(WOff& o, int w, int y, int hx, int 
 constexpr int PR_BX = 32, PR_BY = 4, PR_NT = PR_BX * PR_BY;
 // Resident blocks per SM and the next-plane word prefetch, measured at 256^3 (collide ms, D3Q19 /
 // D3Q27): 4 / 3 blocks with prefetch 0.485 / 0.734 (no spills); 5 / 4 with prefetch 0.461 / 0.603
-// (a few spilled registers); 6 / 5 with prefetch 0.456 / 0.695; 6 / 5 without 0.452 / 0.651.
-// Kept: D3Q19 6 blocks without the prefetch, D3Q27 4 blocks with it.
+// (a few spilled registers); 6 / 5 with prefetch 0.456 / 0.695; 6 / 5 without 0.452 / 0.651; D3Q19
+// without: 5 blocks 0.454, 7 blocks 0.444 (spilling up to 320 bytes).
+// Kept: D3Q19 7 blocks without the prefetch, D3Q27 4 blocks with it.
 #ifndef LBM_PR_MINB19
-#define LBM_PR_MINB19 6
+#define LBM_PR_MINB19 7
 #endif
 #ifndef LBM_PR_MINB27
 #define LBM_PR_MINB27 4
