@@ -106,6 +106,31 @@ def test_fullsize_onepass_equals_two_pass(workload, Q):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("Q", [19, 27])
+def test_fullsize_fp16_paired_layout(workload, Q):
+    # the shifted-FP16 store as the bench runs it (x-paired layout, pair kernels) against the one-cell
+    # layout bit for bit after three steps, and sampled cells against the oracle at the FP16 bound
+    import torch
+    rho, u, wparams = workload
+    d = dict(lattice=Q, shape=SHAPE, store="fp16", **wparams)
+    a = U.run_gpu(d, rho, u, steps=3)
+    fa = a.populations()
+    a.close()
+    b = U.run_gpu(dict(d, store_layout="single"), rho, u, steps=3)
+    fb = b.populations()
+    b.close()
+    assert torch.equal(fa, fb)
+    samples = _samples(rho, seed=Q * 100 + 3)
+    idx = torch.tensor(samples, device=fa.device, dtype=torch.long)
+    fg = fa[:, idx[:, 0], idx[:, 1], idx[:, 2]].double().cpu().numpy()
+    del fa, fb
+    torch.cuda.empty_cache()
+    d32 = dict(lattice=Q, shape=SHAPE, **wparams)
+    for k, c in enumerate(samples[:8]):
+        fo = _oracle_subbox(d32, rho, u, c, 7, 3)
+        assert np.abs(fg[:, k] - fo).max() < 1e-3 * np.abs(fo).max(), tuple(c)
+
+
 def test_largest_domain_near_the_cell_limit():
     # 1290^3 = 2,146,689,000 cells, just under the 2^31 - 1 cells that 32-bit cell offsets allow
     # (D3Q19 populations 163 GB): two steps of a C-S field, sampled cells (among them the last
