@@ -273,13 +273,13 @@ void lbm_destroy(lbm_ctx* ctx);
  * lbm_batch_tune: autotunes each group's launch shape on the live state, in two
  *   stages, by timing the collide launches of every group for trial_steps steps:
  *   first every tile shape (LBM_BATCH_SHAPES) with automatic z-chunks, then, for
- *   the fastest shape, each candidate z-chunk (automatic, 1, 2, 4, 8, 16, 32
- *   planes per block).  A group and the group of the same lattice and physics
+ *   the fastest shape, each candidate z-chunk (automatic, 1, 4, 8, 16, 32 planes
+ *   per block, or a whole column per block).  A group and the group of the same lattice and physics
  *   with the other solid handling share members, so they take one shape (the
  *   one with the least summed time); the z-chunk is per group.  Keeps the
  *   fastest per group and writes its z-chunk to
- *   zchunk_out[g] for g < max_groups (0 = automatic; lbm_batch_group reads the
- *   shape).  The members advance by 12 x (trial_steps + 1) steps.
+ *   zchunk_out[g] for g < max_groups (0 = automatic, 2^30 = whole columns;
+ *   lbm_batch_group reads the shape).  The members advance by 12 x (trial_steps + 1) steps.
  * lbm_batch_info: number of groups, tiles of all launches of one pass, graph mode
  *   (0 not recorded yet, 1 device-side WHILE loop, 2 replayed two-step graph).
  * lbm_batch_group: lattice (19 | 27), solid handling (0 | 1), tile shape and

@@ -22,6 +22,8 @@
 
 using lbm::BatchDom;
 using lbm::BatchDomTable;
+using lbm::BatchRun;
+using lbm::div_magic;
 using lbm::BatchTile;
 using lbm::KParams;
 
@@ -31,7 +33,9 @@ namespace {
 // tile arrays.
 struct Launch {
     BatchDomTable tab{};
-    int t0 = 0, nt = 0;             // tiles (both passes)
+    int t0 = 0, nt = 0;             // collide tiles
+    int p0 = 0, np = 0;             // density/psi tiles (the collide tiles in a solid-handling group)
+    int r0 = 0, nr = 0;             // density/psi runs of whole planes (plain groups)
 };
 
 struct Group {
@@ -41,8 +45,9 @@ struct Group {
     int zchunk = 0;                 // 0 = automatic
     int shape = 0;                  // tile shape: index into lbm::BATCH_SHAPES
     std::vector<Launch> launches;
-    BatchTile* tiles = nullptr;     // tiles of both passes (device)
-    int ntiles = 0;
+    BatchTile* tiles = nullptr;     // collide tiles, then density/psi tiles (device)
+    int ntiles = 0;                 // collide tiles
+    BatchRun* runs = nullptr;       // density/psi runs (device)
 };
 
 __global__ void set_counter_kernel(int* counter, int value) { *counter = value; }
@@ -83,6 +88,8 @@ BatchDom dom_of(const lbm_ctx* c) {
     d.psi = c->psi;
     d.nbmask = c->nbmask;
     d.status = c->status;
+    div_magic((uint32_t)c->kp.nx, d.mx, d.sx);
+    div_magic((uint32_t)c->kp.ny, d.my, d.sy);
     return d;
 }
 
@@ -123,7 +130,9 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
 
 void free_tiles(Group& g) {
     if (g.tiles) cudaFree(g.tiles);
+    if (g.runs) cudaFree(g.runs);
     g.tiles = nullptr;
+    g.runs = nullptr;
     g.ntiles = 0;
     g.launches.clear();
 }
@@ -135,6 +144,7 @@ void drop_graph(lbm_batch* b) {
     b->graph_mode = 0;
 }
 
+constexpr int ZC_WHOLE = 1 << 30;   // a z-chunk candidate: every column marches through all its planes
 constexpr int ZC_AUTO_MAX = 32;   // automatic z-chunks: longer marches gain little, and in a mix of
                                   // uneven members shorter blocks balance the last wave
 
@@ -181,33 +191,75 @@ lbm_status member_tile_flags(lbm_batch* b, lbm_ctx* c, int tw, int th) {
 // resident blocks (or the group's fixed zchunk).  A member with solids contributes its solid-free
 // chunks to the group without solid handling and the others to the solid group of its physics,
 // so only cells near solids pay for the solid tests.
+//
+// Where a row leaves 1 .. 16 cells past its last full tile width (tw = 32), those cells form narrow
+// columns, 16 cells wide and twice as high, which the same blocks step (BatchTile::narrow): a
+// 32-wide tile there would leave 16 to 31 of its 32 lanes per row idle.
+//
+// The density/psi pass of a group without solid handling covers the planes in which no column needs
+// it (every plane of a member without solids) as runs of RUN_CELLS consecutive cells, and only the
+// solid-free columns of the other planes as tiles: the pass needs no stencil, so nothing ties its
+// threads to rows, and rows that do not fill a tile's width leave no lanes idle.
+#ifndef LBM_BATCH_RUNS
+#define LBM_BATCH_RUNS 1
+#endif
+#ifndef LBM_BATCH_NARROW
+#define LBM_BATCH_NARROW 1
+#endif
+#ifndef LBM_BATCH_LPT
+#define LBM_BATCH_LPT 1
+#endif
+constexpr uint32_t RUN_CELLS = 2048;
+
+struct Column {
+    int x0, y0, w, h, narrow;
+};
+
+// the columns of a member for tiles tw x th: full-width columns, then the narrow ones (if any)
+std::vector<Column> member_columns(const KParams& k, int tw, int th) {
+    std::vector<Column> cols;
+    const int r = k.nx % tw;
+    const bool narrow = LBM_BATCH_NARROW && tw > lbm::BATCH_NARROW_BX && r > 0 && r <= lbm::BATCH_NARROW_BX;
+    const int wmain = narrow ? k.nx - r : k.nx;
+    for (int y0 = 0; y0 < k.ny; y0 += th)
+        for (int x0 = 0; x0 < wmain; x0 += tw) cols.push_back({x0, y0, tw, th, 0});
+    if (narrow) {
+        const int hn = tw * th / lbm::BATCH_NARROW_BX;
+        for (int y0 = 0; y0 < k.ny; y0 += hn) cols.push_back({wmain, y0, lbm::BATCH_NARROW_BX, hn, 1});
+    }
+    return cols;
+}
+
 lbm_status build_tiles(lbm_batch* b, Group& g) {
     free_tiles(g);
     if (g.shape < 0 || g.shape >= lbm::BATCH_NSHAPES) return bfail(b, LBM_ERR_ARG, "unknown tile shape");
     const lbm::BatchShape& sh = lbm::BATCH_SHAPES[g.shape];
     const int tw = sh.bx, th = sh.by;
+    const int fw = lbm::BATCH_NARROW_BX, fh = th;   // mask flags grid: both column kinds are unions of its cells
     const int resident = g.Q == 19 ? sh.minb19 : sh.minb27;
-    long long cols = 0;
-    for (int d : g.members) {
-        const KParams& k = b->members[d]->kp;
-        cols += (long long)((k.nx + tw - 1) / tw) * ((k.ny + th - 1) / th);
-    }
+    const bool use_runs = LBM_BATCH_RUNS && !g.solids;
+    long long ncols = 0;
+    for (int d : g.members) ncols += (long long)member_columns(b->members[d]->kp, tw, th).size();
     const long long target = 152LL * resident * 4;
-    const long long chunks_auto = std::max(1LL, (target + cols - 1) / std::max(cols, 1LL));
-    std::vector<BatchTile> t;
-    std::vector<uint8_t> need;   // per plane of one column: needs solid handling
+    const long long chunks_auto = std::max(1LL, (target + ncols - 1) / std::max(ncols, 1LL));
+    std::vector<BatchTile> t, pt;   // collide tiles; density/psi tiles
+    std::vector<BatchRun> runs;
+    std::vector<uint8_t> need;      // per plane of one column: needs solid handling
+    std::vector<uint8_t> mixed;     // per plane: some column needs solid handling
     for (size_t j = 0; j < g.members.size(); ++j) {
         const int d = (int)(j % lbm::BATCH_LAUNCH_DOMS);   // slot in the launch's member table
         if (d == 0) {
             g.launches.emplace_back();
             g.launches.back().t0 = (int)t.size();
+            g.launches.back().p0 = (int)pt.size();
+            g.launches.back().r0 = (int)runs.size();
         }
         Launch& L = g.launches.back();
         L.tab.d[d] = b->table[g.members[j]];
         lbm_ctx* c = b->members[g.members[j]];
         const KParams& k = c->kp;
         const bool solid_work = has_solid_work(c);
-        lbm_status fs = member_tile_flags(b, c, tw, th);
+        lbm_status fs = member_tile_flags(b, c, fw, fh);
         if (fs != LBM_OK) return fs;
         int zc;
         if (g.zchunk > 0) zc = std::min(g.zchunk, k.nz);            // the batch's tuned choice
@@ -216,41 +268,103 @@ lbm_status build_tiles(lbm_batch* b, Group& g) {
             const long long ch = std::min<long long>(chunks_auto, k.nz);
             zc = std::min(ZC_AUTO_MAX, (int)((k.nz + ch - 1) / ch));
         }
-        const int nxb = (k.nx + tw - 1) / tw, nyb = (k.ny + th - 1) / th;
-        const int member_t0 = (int)t.size() - L.t0;
+        const int nxf = (k.nx + fw - 1) / fw, nyf = (k.ny + fh - 1) / fh;
+        const std::vector<Column> cols = member_columns(k, tw, th);
+        auto column_needs = [&](const Column& col) {
+            const bool side = (k.wall_x && (col.x0 == 0 || col.x0 + col.w >= k.nx)) ||
+                              (k.wall_y && (col.y0 == 0 || col.y0 + col.h >= k.ny));
+            const int fx0 = col.x0 / fw, fx1 = std::min(nxf, (col.x0 + col.w + fw - 1) / fw);
+            const int fy0 = col.y0 / fh, fy1 = std::min(nyf, (col.y0 + col.h + fh - 1) / fh);
+            for (int z = 0; z < k.nz; ++z) {
+                bool s2 = side || (k.wall_z && (z == 0 || z == k.nz - 1));
+                if (c->nbmask)
+                    for (int fy = fy0; fy < fy1 && !s2; ++fy)
+                        for (int fx = fx0; fx < fx1 && !s2; ++fx)
+                            s2 = c->tile_flags[((size_t)z * nyf + fy) * nxf + fx] != 0;
+                need[z] = s2 ? 1 : 0;
+            }
+        };
         need.resize(k.nz);
-        for (int yb = 0; yb < nyb; ++yb)
-            for (int xb = 0; xb < nxb; ++xb) {
-                const int x0 = xb * tw, y0 = yb * th;
-                const bool side = (k.wall_x && (x0 == 0 || x0 + tw >= k.nx)) ||
-                                  (k.wall_y && (y0 == 0 || y0 + th >= k.ny));
-                for (int z = 0; z < k.nz; ++z) {
-                    bool s = side || (k.wall_z && (z == 0 || z == k.nz - 1));
-                    if (c->nbmask) s = s || c->tile_flags[((size_t)z * nyb + yb) * nxb + xb] != 0;
-                    need[z] = s ? 1 : 0;
-                }
+        mixed.assign(k.nz, 0);
+        if (solid_work)
+            for (const Column& col : cols) {
+                column_needs(col);
+                for (int z = 0; z < k.nz; ++z) mixed[z] |= need[z];
+            }
+        const int member_t0 = (int)t.size() - L.t0, member_p0 = (int)pt.size() - L.p0;
+        for (const Column& col : cols) {
+            column_needs(col);
+            for (int z0 = 0; z0 < k.nz;) {
+                int z1 = z0 + 1;
+                while (z1 < k.nz && need[z1] == need[z0] && z1 - z0 < zc) ++z1;
+                const bool mine = solid_work ? (need[z0] != 0) == (g.solids != 0) : true;
+                if (mine) t.push_back({d, col.x0, col.y0, z0, z1 - z0, col.narrow});
+                z0 = z1;
+            }
+            if (use_runs)   // density/psi tiles: this column's solid-free planes among the mixed ones
                 for (int z0 = 0; z0 < k.nz;) {
+                    if (need[z0] || !mixed[z0]) {
+                        ++z0;
+                        continue;
+                    }
                     int z1 = z0 + 1;
-                    while (z1 < k.nz && need[z1] == need[z0] && z1 - z0 < zc) ++z1;
-                    const bool mine = solid_work ? (need[z0] != 0) == (g.solids != 0) : true;
-                    if (mine) t.push_back({d, x0, y0, z0, z1 - z0});
+                    while (z1 < k.nz && !need[z1] && mixed[z1] && z1 - z0 < zc) ++z1;
+                    pt.push_back({d, col.x0, col.y0, z0, z1 - z0, col.narrow});
                     z0 = z1;
                 }
-            }
+        }
         // z-chunk-major order within the member (as the single-domain grid): blocks resident at
         // the same time work on neighbouring columns of the same planes
-        std::stable_sort(t.begin() + L.t0 + member_t0, t.end(), [](const BatchTile& a, const BatchTile& b2) {
+        auto zmajor = [](const BatchTile& a, const BatchTile& b2) {
             return a.z0 != b2.z0 ? a.z0 < b2.z0 : (a.y0 != b2.y0 ? a.y0 < b2.y0 : a.x0 < b2.x0);
-        });
+        };
+        std::stable_sort(t.begin() + L.t0 + member_t0, t.end(), zmajor);
+        std::stable_sort(pt.begin() + L.p0 + member_p0, pt.end(), zmajor);
+        if (use_runs) {
+            const uint32_t nxy = (uint32_t)k.nx * (uint32_t)k.ny;
+            for (int z0 = 0; z0 < k.nz;) {
+                if (mixed[z0]) {
+                    ++z0;
+                    continue;
+                }
+                int z1 = z0 + 1;
+                while (z1 < k.nz && !mixed[z1]) ++z1;
+                const uint32_t end = (uint32_t)z1 * nxy;
+                for (uint32_t a = (uint32_t)z0 * nxy; a < end; a += std::min(RUN_CELLS, end - a))
+                    runs.push_back({d, a, a + std::min(RUN_CELLS, end - a)});
+                z0 = z1;
+            }
+        }
         L.nt = (int)t.size() - L.t0;
+        L.np = (int)pt.size() - L.p0;
+        L.nr = (int)runs.size() - L.r0;
     }
-    if (t.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
-    if (!t.empty()) {
-        BCK(b, cudaMalloc((void**)&g.tiles, t.size() * sizeof(BatchTile)));
-        BCK(b, cudaMemcpyAsync(g.tiles, t.data(), t.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    // longest marches first within a launch: blocks start roughly in index order, so the short ones
+    // fill the last wave instead of a few long ones running on alone
+    if (LBM_BATCH_LPT)
+        for (const Launch& L : g.launches)
+            std::stable_sort(t.begin() + L.t0, t.begin() + L.t0 + L.nt,
+                             [](const BatchTile& a, const BatchTile& b2) { return a.zc > b2.zc; });
+    if (!use_runs)
+        for (Launch& L : g.launches) {   // the density/psi pass runs over the collide tiles
+            L.p0 = L.t0;
+            L.np = L.nt;
+        }
+    else
+        for (Launch& L : g.launches) L.p0 += (int)t.size();
+    if (t.size() + pt.size() > 0x7fffffff || runs.size() > 0x7fffffff) return bfail(b, LBM_ERR_ARG, "too many tiles");
+    const size_t nt = t.size() + pt.size();
+    if (nt > 0) {
+        t.insert(t.end(), pt.begin(), pt.end());
+        BCK(b, cudaMalloc((void**)&g.tiles, nt * sizeof(BatchTile)));
+        BCK(b, cudaMemcpyAsync(g.tiles, t.data(), nt * sizeof(BatchTile), cudaMemcpyHostToDevice, b->stream));
+    }
+    if (!runs.empty()) {
+        BCK(b, cudaMalloc((void**)&g.runs, runs.size() * sizeof(BatchRun)));
+        BCK(b, cudaMemcpyAsync(g.runs, runs.data(), runs.size() * sizeof(BatchRun), cudaMemcpyHostToDevice, b->stream));
     }
     BCK(b, cudaStreamSynchronize(b->stream));
-    g.ntiles = (int)t.size();
+    g.ntiles = (int)(nt - pt.size());
     return LBM_OK;
 }
 
@@ -268,9 +382,12 @@ cudaError_t collide_group(const Group& g, int parity, cudaStream_t st) {
 cudaError_t psi_group(const Group& g, int parity, cudaStream_t st) {
     if (!g.phys.multiphase) return cudaSuccess;
     for (const Launch& L : g.launches) {
-        const BatchTile* t = g.tiles + L.t0;   // the collide tiles (same shape, same split)
-        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st)
-                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.nt, parity, g.solids, g.shape, st);
+        const BatchTile* t = g.tiles + L.p0;
+        cudaError_t e = g.Q == 19 ? lbm::launch_psi_batch_q19(g.phys, L.tab, t, L.np, parity, g.solids, g.shape, st)
+                                  : lbm::launch_psi_batch_q27(g.phys, L.tab, t, L.np, parity, g.solids, g.shape, st);
+        if (e == cudaSuccess && L.nr > 0)
+            e = g.Q == 19 ? lbm::launch_psi_runs_q19(g.phys, L.tab, g.runs + L.r0, L.nr, parity, st)
+                          : lbm::launch_psi_runs_q27(g.phys, L.tab, g.runs + L.r0, L.nr, parity, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -605,7 +722,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t trial_steps, int32_t* zchunk_out
         }
     }
     // stage 2: the z-chunks for the chosen shapes, per group
-    const int zc[] = {0, 1, 2, 4, 8, 16, 32};
+    const int zc[] = {0, 1, 4, 8, 16, 32, ZC_WHOLE};
     const int nz = (int)(sizeof(zc) / sizeof(zc[0]));
     r = time_candidates(
         b, trial_steps, nz, [&](int k, int) { return shape[k]; }, [&](int, int ci) { return zc[ci]; }, t);

@@ -93,8 +93,47 @@ __global__ void __launch_bounds__(BatchTileShape<S>::NT) psi_batch_kernel(const 
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
-    psi_column<PARITY, SOLIDS, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + threadIdx.x,
-                                      t.y0 + threadIdx.y, t.z0, min(t.z0 + t.zc, m.nz), nullptr, nullptr);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int w = t.narrow ? BATCH_NARROW_BX : (int)blockDim.x;   // a narrow tile: 16 cells wide
+    psi_column<PARITY, SOLIDS, false>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0 + tid % w, t.y0 + tid / w, t.z0,
+                                      min(t.z0 + t.zc, m.nz), nullptr, nullptr);
+}
+
+// multi-domain density + psi pass over runs of whole planes (cells without solid handling): thread k
+// of a block takes cells begin + k, begin + k + RUN_NT, ... of its run, so rows of any length pack
+// the warps densely.  Per cell the arithmetic and its order are psi_column's.
+constexpr int RUN_NT = 256;
+__device__ __forceinline__ uint32_t div_by_magic(uint32_t n, uint32_t m, int s) {
+    return (uint32_t)(((unsigned long long)m * n) >> s);
+}
+template <int PARITY>
+__global__ void __launch_bounds__(RUN_NT) psi_run_kernel(const KParams phys, const __grid_constant__ BatchDomTable tab,
+                                                         const BatchRun* __restrict__ runs) {
+    const BatchRun r = runs[blockIdx.x];
+    const BatchDom& m = tab.d[r.d];
+    const PlaneIdx32 addr{m.base, (uint32_t)m.plane};
+    const uint32_t nx = (uint32_t)m.nx, ny = (uint32_t)m.ny, nz = (uint32_t)m.nz, nxy = nx * ny;
+    for (uint32_t c = r.begin + threadIdx.x; c < r.end; c += RUN_NT) {
+        const uint32_t row = div_by_magic(c, m.mx, m.sx), x = c - row * nx;
+        const uint32_t z = div_by_magic(row, m.my, m.sy), y = row - z * ny;
+        Off32 o;
+        o.xo[0] = (uint32_t)wrap1((int)x - 1, (int)nx);
+        o.xo[1] = x;
+        o.xo[2] = (uint32_t)wrap1((int)x + 1, (int)nx);
+        o.yo[0] = (uint32_t)wrap1((int)y - 1, (int)ny) * nx;
+        o.yo[1] = y * nx;
+        o.yo[2] = (uint32_t)wrap1((int)y + 1, (int)ny) * nx;
+        o.zo[0] = (uint32_t)wrap1((int)z - 1, (int)nz) * nxy;
+        o.zo[1] = z * nxy;
+        o.zo[2] = (uint32_t)wrap1((int)z + 1, (int)nz) * nxy;
+        o.c = c;
+        float p[Q];
+        gather32<Q, PARITY, false>(addr, o, 0u, p);
+        float rho = 0.0f;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rho += p[i];
+        m.psi[bounded(c, (unsigned long long)nxy * nz)] = eval_psi(phys, rho, m.status);
+    }
 }
 
 // ---- fused collide-stream pass: psi tile -> forces -> gather -> moments -> relax -> M^-1 -> store
@@ -179,12 +218,16 @@ __device__ __forceinline__ void put_psi_plane(float* slot, const float (&v)[TS::
 // PSI_PF: the psi (and FP16 density) ring planes are loaded into registers one plane ahead and
 // stored into the ring at the next plane (all but the multi-domain kernels' solid tiles, which
 // have no registers to spare and load each plane just before its barrier).
-template <class TS, int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A>
+template <class TS, int PARITY, bool SOLIDS, bool MULTIPHASE, bool F16, bool PSI_PF, class GM, class A,
+          bool FLAT = false>
 __device__ __forceinline__ void collide_tile(const KParams& kp, const GM& g, const A& addr, const float* __restrict__ psi,
                                              const uint32_t* __restrict__ nbmask, unsigned* status, int x0, int y0,
                                              int z0, int zchunk, int zmax, float (*ring)[TS::RP], float (*rring)[TS::RP],
                                              const float* __restrict__ rsrc, const float* __restrict__ rown) {
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TS::BX * ty;
+    // FLAT: the block has another shape with as many threads (a narrow multi-domain tile); its threads
+    // take the tile's cells in row-major order
+    const int tid = FLAT ? (int)(threadIdx.x + blockDim.x * threadIdx.y) : (int)(threadIdx.x + TS::BX * threadIdx.y);
+    const int tx = FLAT ? tid % TS::BX : (int)threadIdx.x, ty = FLAT ? tid / TS::BX : (int)threadIdx.y;
     const int x = x0 + tx, y = y0 + ty;
     const int nx = g.nx(), ny = g.ny(), nz = g.nz();
     const bool act_xy = x < nx && y < ny;
@@ -970,13 +1013,21 @@ template <int PARITY, bool SOLIDS, bool MULTIPHASE, int S>
 __global__ void __launch_bounds__(BatchTileShape<S>::NT, batch_minb<S>()) collide_batch_kernel(
         const KParams phys, const __grid_constant__ BatchDomTable tab, const BatchTile* __restrict__ tiles) {
     using TS = BatchTileShape<S>;
+    using TN = TileShape<BATCH_NARROW_BX, TS::NT / BATCH_NARROW_BX>;   // narrow tiles at the ends of rows
+    static_assert(TN::RP <= TS::RP, "a narrow tile's ring fits the block's");
     __shared__ float ring[4][TS::RP];
     const BatchTile t = tiles[blockIdx.x];
     const BatchDom& m = tab.d[t.d];
     const DGeom g{m};
     const DomPlanes addr{m};
-    collide_tile<TS, PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0,
-                                                                t.z0, t.zc, g.nz(), ring, nullptr, nullptr, nullptr);
+    if (TS::BX != BATCH_NARROW_BX && t.narrow)
+        collide_tile<TN, PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS, DGeom, DomPlanes, true>(
+            phys, g, addr, m.psi, m.nbmask, m.status, t.x0, t.y0, t.z0, t.zc, g.nz(),
+            reinterpret_cast<float (*)[TN::RP]>(&ring[0][0]), nullptr, nullptr, nullptr);
+    else
+        collide_tile<TS, PARITY, SOLIDS, MULTIPHASE, false, !SOLIDS>(phys, g, addr, m.psi, m.nbmask, m.status, t.x0,
+                                                                    t.y0, t.z0, t.zc, g.nz(), ring, nullptr, nullptr,
+                                                                    nullptr);
 }
 
 // ---- initialisation: f_bar = M^-1 m^eq(rho, u) (Eq. e13), natural layout
@@ -1462,6 +1513,14 @@ cudaError_t LBM_CAT(launch_collide_batch_q, LBM_Q)(const KParams& phys, const Ba
         case 4: return launch_collide_batch_shape<4>(phys, doms, tiles, ntiles, key, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t LBM_CAT(launch_psi_runs_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms, const BatchRun* runs,
+                                              int nruns, int parity, cudaStream_t st) {
+    if (nruns <= 0) return cudaSuccess;
+    if (parity == 0) psi_run_kernel<0><<<nruns, RUN_NT, 0, st>>>(phys, doms, runs);
+    else psi_run_kernel<1><<<nruns, RUN_NT, 0, st>>>(phys, doms, runs);
+    return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_psi_batch_q, LBM_Q)(const KParams& phys, const BatchDomTable& doms,

@@ -60,6 +60,26 @@ struct BatchDom {
     float* psi;
     const uint32_t* nbmask;
     unsigned* status;
+    uint32_t mx, my;              // n / nx and n / ny as (n * m) >> s for n < 2^31 (div_magic)
+    int sx, sy;
+};
+
+// Division by an invariant d in [1, 2^31) as a multiply and a shift (Granlund and Montgomery, PLDI
+// 1994, Thm. 4.2, with N = 31): l = ceil(log2 d), m = ceil(2^(31 + l) / d), s = 31 + l; then
+// floor(n / d) = (n * m) >> s for every n < 2^31, and m < 2^32.
+inline void div_magic(uint32_t d, uint32_t& m, int& s) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    m = (uint32_t)(((1ull << (31 + l)) + d - 1) / d);
+    s = 31 + l;
+}
+
+// A run of cells [begin, end) of member d of a multi-domain launch (cell index (z ny + y) nx + x),
+// none of which needs solid handling: the density/psi pass covers whole planes of a member this way,
+// one block per run, with no lanes left idle at the ends of rows.
+struct BatchRun {
+    int d;
+    uint32_t begin, end;
 };
 
 // Members of one multi-domain launch.  The table travels in the kernel parameters (constant bank),
@@ -70,9 +90,12 @@ struct BatchDomTable {
 };
 
 // One block of a multi-domain launch: member d of the launch's table, cells [x0, x0+tile width) x
-// [y0, y0+tile height) x [z0, z0+zc) (clipped to the domain).
+// [y0, y0+tile height) x [z0, z0+zc) (clipped to the domain).  narrow = 1: the tile is
+// BATCH_NARROW_BX cells wide and (threads / BATCH_NARROW_BX) high instead of the launch's shape --
+// the last columns of rows whose length leaves at most that many cells past the last full tile.
+constexpr int BATCH_NARROW_BX = 16;
 struct BatchTile {
-    int d, x0, y0, z0, zc;
+    int d, x0, y0, z0, zc, narrow;
 };
 
 // Tile shapes of the multi-domain kernels, compiled for each lattice; lbm_batch_tune picks one per
@@ -122,6 +145,8 @@ struct Bufs {
     cudaError_t launch_psi_batch_q##Q(const KParams& phys, const BatchDomTable& tab,                 \
                                       const BatchTile* tiles, int ntiles, int parity, int solids,      \
                                       int shape, cudaStream_t st);                                    \
+    cudaError_t launch_psi_runs_q##Q(const KParams& phys, const BatchDomTable& tab, const BatchRun* runs, \
+                                     int nruns, int parity, cudaStream_t st);                          \
     cudaError_t launch_contact_q##Q(const KParams& kp, int parity, const Bufs& B, float thr, int* out, \
                                     cudaStream_t st);                                               \
     cudaError_t launch_onepass_q##Q(const KParams& kp, unsigned* status, cudaStream_t st);          \

@@ -174,6 +174,31 @@ def test_single_domain_tile_path_equals_grid_path(which):
 
 
 @pytest.mark.parametrize("Q", [19, 27])
+@pytest.mark.parametrize("nx", [33, 44, 48])
+def test_narrow_columns_next_to_walls_and_solids(Q, nx):
+    # nx = 32 + 1 .. 16: the last cells of every row step in 16-wide tiles; here they touch a wall in
+    # x (walls on every face) and a solid cylinder crosses them.  The one-member batch (tiles,
+    # solid handling only where needed) equals the whole-grid kernels (solid handling everywhere) bit
+    # for bit, and both follow the oracle.
+    kw, rl, rv = U.cs_eos("T0.7")
+    shape = (nx, 14, 10)
+    rho, u = W.droplet(shape, 4.0, rl, rv)
+    z, y, x = np.meshgrid(np.arange(10), np.arange(14), np.arange(nx), indexing="ij")
+    solid = ((x - (nx - 5)) ** 2 + (y - 7) ** 2 <= 2.5 ** 2).astype(np.uint8)   # a post along z near x = nx
+    d = dict(lattice=Q, shape=shape, bc=(1, 1, 1), sigma=0.1, kappa=0.3, G_ads=0.05, **kw)
+    tiles = U.run_gpu(d, rho, u, solid)
+    grid = U.run_gpu(d, rho, u, solid)
+    grid.set_kernel_timing(True)
+    for n in (3, 20):
+        tiles.step(n)
+        grid.step(n)
+        assert np.array_equal(tiles.populations().cpu().numpy(), grid.populations().cpu().numpy()), n
+    ref = U.run_oracle(d, rho, u, solid, steps=23)
+    er, eu, _, _ = U.compare_moments(tiles, ref)
+    assert er < 1e-4 and eu < 1e-4, (er, eu)
+
+
+@pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("shape,zchunk", [((40, 20, 3), 0), ((33, 17, 26), 0), ((33, 17, 26), 5)])
 def test_zwall_domain_split_equals_batch(Q, shape, zchunk):
     # a domain with walls only at the z ends steps its inner planes with the solid-free kernel and
