@@ -390,6 +390,30 @@ constexpr uint32_t PERM_KEEP = 0x3210u, PERM_SWAP = 0x1032u;   // __byte_perm se
 __device__ __forceinline__ float half_lo(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
 __device__ __forceinline__ float half_hi(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
 
+// slot words of the paired FP16 store: read once and written once per step
+#ifndef LBM_LDWORD_HINT
+#define LBM_LDWORD_HINT 0
+#endif
+#ifndef LBM_STWORD_CS
+#define LBM_STWORD_CS 0
+#endif
+__device__ __forceinline__ uint32_t ldword(const uint32_t* p) {
+#if LBM_LDWORD_HINT == 2
+    uint32_t v;
+    asm("ld.global.nc.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+#else
+    return __ldg(p);
+#endif
+}
+__device__ __forceinline__ void stword(uint32_t* p, uint32_t v) {
+#if LBM_STWORD_CS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 // AA gather of a pair's slot words (the paired counterpart of gather32); selL / selR exchange the
 // halves of words fetched across the left / right end of the row
 template <int PARITY, bool SOLIDS>
@@ -398,9 +422,9 @@ __device__ __forceinline__ void gather_pair(const WordPlanes& a, const WOff& o, 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0 || (SOLIDS && ((bits >> OPP(i)) & 1u))) {
-            w[i] = __ldg(a.ptr(i, o.c));
+            w[i] = ldword(a.ptr(i, o.c));
         } else {
-            const uint32_t v = __ldg(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
+            const uint32_t v = ldword(a.ptr(OPP(i), o.nb(-EX(i), -EY(i), -EZ(i))));
             w[i] = EX(i) > 0 ? __byte_perm(v, 0u, selL) : (EX(i) < 0 ? __byte_perm(v, 0u, selR) : v);
         }
     }
@@ -413,10 +437,10 @@ __device__ __forceinline__ void store_pair(const WordPlanes& a, const WOff& o, u
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (PARITY == 0 || i == 0 || (SOLIDS && ((bits >> i) & 1u))) {
-            *a.ptr(OPP(i), o.c) = w[i];
+            stword(a.ptr(OPP(i), o.c), w[i]);
         } else {
             const uint32_t v = EX(i) > 0 ? __byte_perm(w[i], 0u, selR) : (EX(i) < 0 ? __byte_perm(w[i], 0u, selL) : w[i]);
-            *a.ptr(i, o.nb(EX(i), EY(i), EZ(i))) = v;
+            stword(a.ptr(i, o.nb(EX(i), EY(i), EZ(i))), v);
         }
     }
 }
