@@ -390,12 +390,14 @@ constexpr uint32_t PERM_KEEP = 0x3210u, PERM_SWAP = 0x1032u;   // __byte_perm se
 __device__ __forceinline__ float half_lo(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
 __device__ __forceinline__ float half_hi(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
 
-// slot words of the paired FP16 store: read once and written once per step
+// slot words of the paired FP16 store: read once and written once per step.  Measured at 256^3 (step
+// ms, D3Q19 / D3Q27, two repetitions): plain loads and stores 0.6453 / 0.8782; loads with a 256-byte L2
+// prefetch 0.6420 / 0.8748; evict-first stores 0.6406 / 0.8777; both 0.6375 / 0.8745 (kept).
 #ifndef LBM_LDWORD_HINT
-#define LBM_LDWORD_HINT 0
+#define LBM_LDWORD_HINT 2
 #endif
 #ifndef LBM_STWORD_CS
-#define LBM_STWORD_CS 0
+#define LBM_STWORD_CS 1
 #endif
 __device__ __forceinline__ uint32_t ldword(const uint32_t* p) {
 #if LBM_LDWORD_HINT == 2
