@@ -101,7 +101,13 @@ def test_per_lattice_launch_helpers_have_internal_linkage(lib):
         parts = r.split(None, 2)
         if len(parts) < 3 or parts[1] not in ("T", "W", "V", "D", "B", "R", "u"):
             continue
-        m = re.search(r"(?:^|[\s*&])lbm::(\w+)", parts[2].split("(")[0])
+        # the function's own qualified name: template arguments removed (a standard-library template
+        # instantiated for an lbm type is not an lbm function), the name last before its parameters
+        name = parts[2].split("(")[0]
+        prev = None
+        while prev != name:
+            prev, name = name, re.sub(r"<[^<>]*>", "", name)
+        m = re.search(r"(?:^|[\s*&])lbm::(\w+)$", name.strip())
         if not m:
             continue
         checked += 1
