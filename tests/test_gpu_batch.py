@@ -173,6 +173,35 @@ def test_single_domain_tile_path_equals_grid_path(which):
     assert launches["collide"] == 47 and launches["psi"] == 47
 
 
+def test_groups_larger_than_one_launch():
+    # 70 members of one physics with walls in z: the solid-free and the solid-handling group each hold
+    # 70 members, more than one launch's member table (64), so each pass runs two launches per group,
+    # with their own collide tiles, density tiles and density runs (widths 33 / 40 / 47 add narrow
+    # columns).  Every member evolves bitwise as when stepped alone.
+    from paper_2306_16274_gb300 import Batch
+    kw, rl, rv = U.cs_eos("T0.7")
+    members = []
+    for k in range(70):
+        shape = (33 + 7 * (k % 3), 9 + k % 4, 6 + k % 3)
+        rho, u = W.droplet(shape, 2.5 + 0.5 * (k % 2), rl, rv)
+        members.append((dict(lattice=19, shape=shape, bc=(0, 0, 1), sigma=0.1, kappa=0.3, G_ads=0.05, **kw), rho, u,
+                        None))
+    alone = _make(members)
+    together = _make(members)
+    b = Batch(together)
+    assert b.info()["groups"] == 2
+    for n in (1, 5):
+        b.step(n)
+        b.sync()
+        for a in alone:
+            a.step(n)
+        for k, (a, t) in enumerate(zip(alone, together)):
+            assert np.array_equal(a.populations().cpu().numpy(), t.populations().cpu().numpy()), (k, n)
+    b.close()
+    for sim in alone + together:
+        sim.close()
+
+
 @pytest.mark.parametrize("Q", [19, 27])
 @pytest.mark.parametrize("nx", [33, 44, 48])
 def test_narrow_columns_next_to_walls_and_solids(Q, nx):
