@@ -131,6 +131,45 @@ def test_fullsize_fp16_paired_layout(workload, Q):
         assert np.abs(fg[:, k] - fo).max() < 1e-3 * np.abs(fo).max(), tuple(c)
 
 
+def test_fullsize_batch_equals_jobs_stepped_alone():
+    # the batched workload in the configuration bench.py times (64 jobs, 105.7 M cells, edges 48-160,
+    # both lattices, periodic droplets and impacts on a wall), tuned and stepped as one batch: every
+    # job's populations equal those of the job stepped alone, bit for bit (compared on the device)
+    import torch
+
+    from paper_2306_16274_gb300 import Batch, Params, Simulation
+    jobs = bench.batch_jobs(64)
+
+    def make():
+        out = []
+        for params, rho, u in jobs:
+            s = Simulation(Params(**params))
+            s.init_fields(torch.tensor(rho, dtype=torch.float32, device="cuda"),
+                          torch.tensor(u, dtype=torch.float32, device="cuda"))
+            out.append(s)
+        return out
+
+    together = make()
+    b = Batch(together)
+    b.tune(trial_steps=1)
+    b.step(5)
+    b.sync()
+    b.close()
+    total = together[0].step_count
+    assert total == 12 * 2 + 5
+    for k, t in enumerate(together):
+        fb = t.populations()
+        t.close()
+        a = Simulation(Params(**jobs[k][0]))
+        a.init_fields(torch.tensor(jobs[k][1], dtype=torch.float32, device="cuda"),
+                      torch.tensor(jobs[k][2], dtype=torch.float32, device="cuda"))
+        a.step(total)
+        assert torch.equal(a.populations(), fb), k
+        a.close()
+        del fb
+    torch.cuda.empty_cache()
+
+
 def test_largest_domain_near_the_cell_limit():
     # 1290^3 = 2,146,689,000 cells, just under the 2^31 - 1 cells that 32-bit cell offsets allow
     # (D3Q19 populations 163 GB): two steps of a C-S field, sampled cells (among them the last
