@@ -248,6 +248,12 @@ def test_config2_copy_64(Q):
     assert er < TOL_MULTI and eu < TOL_MULTI, (er, eu)
     assert abs(sg[0] - so[0]) < 1e-6 * so[0]
     assert U.momentum_error(sg, so, ref) < TOL_MULTI
+    # the shifted-FP16 store on the same case (x-paired layout: nx even, x periodic) against the same
+    # oracle run, at the storage-precision bounds of tests/test_gpu_fp16.py
+    sim16 = U.run_gpu(dict(d, store="fp16"), rho, u, steps=100)
+    er16, eu16, sg16, _ = U.compare_moments(sim16, ref)
+    assert er16 < 1e-3 and eu16 < 3e-3, (er16, eu16)
+    assert abs(sg16[0] - so[0]) < 1e-4 * so[0]
 
 
 @pytest.mark.parametrize("Q", [19, 27])
